@@ -1,0 +1,84 @@
+"""The oracle time loop: pull-stream, collide, diagnostics.
+
+Test infrastructure (see the package docstring).
+
+State convention (shared with the CUDA library's interface, not its code): ``s[i, z, y, x]``
+holds the post-collision transformed population of cell (x, y, z) in direction i, as plain
+float64 values f (the library stores d = f / w_i - 1 in its storage type). One step pulls
+g = stream(s) and stores s <- collide(g).
+"""
+import torch
+
+from .lattice import DT, get as get_lattice
+from . import collision as C
+from . import stream as ST
+from . import les as L
+
+
+class OracleSim:
+    def __init__(self, lattice, nx, ny, nz=1, params=None, bc=("periodic",) * 3,
+                 wall_velocity=None, van_driest=None):
+        """van_driest = (A_plus, u_tau / nu_0) damps C_s by the distance to the y walls."""
+        self.lat = get_lattice(lattice) if isinstance(lattice, str) else lattice
+        if self.lat.d == 2 and nz != 1:
+            raise ValueError("D2Q9 needs nz = 1")
+        self.shape = (nz, ny, nx)
+        self.p = params if params is not None else C.Params()
+        self.bc = tuple(bc)
+        if wall_velocity is None:
+            wall_velocity = [[[0.0] * 3 for _ in range(2)] for _ in range(3)]
+        self.uw = wall_velocity
+        self.F = torch.zeros((3,) + self.shape, dtype=DT)
+        self.cs_eff = None
+        if van_driest is not None and self.p.cs_smag > 0.0:
+            aplus, utau_nu = van_driest
+            self.cs_eff = L.van_driest_cs(self.p.cs_smag, ny, nz, nx, aplus, utau_nu, wall_axis=1)
+        self.s = torch.zeros((self.lat.Q,) + self.shape, dtype=DT)
+
+    # ---- set-up -------------------------------------------------------------------
+    def set_force(self, uniform=(0.0, 0.0, 0.0), field=None):
+        if field is not None:
+            self.F = torch.as_tensor(field, dtype=DT).reshape((3,) + self.shape).clone()
+        else:
+            self.F = torch.zeros((3,) + self.shape, dtype=DT)
+            for d in range(3):
+                self.F[d] += float(uniform[d])
+
+    def init(self, rho=None, u=None):
+        """Pre-collision field fbar = f^M(rho, u) - S/2 (paper silent on initialisation)."""
+        rho = torch.ones(self.shape, dtype=DT) if rho is None else torch.as_tensor(rho, dtype=DT).reshape(self.shape)
+        u = torch.zeros((3,) + self.shape, dtype=DT) if u is None else torch.as_tensor(u, dtype=DT).reshape((3,) + self.shape)
+        if self.p.reduced_compressibility:
+            # Sec. 10: the momentum is rho0 u, so the equilibrium is centred on rho0 u / rho
+            u = u * (self.p.rho0 / rho)
+        fbar = C.equilibrium(rho, u, self.F, self.lat)
+        self.s = ST.unstream(fbar, self.lat, self.bc, self.uw)
+
+    def set_state(self, s):
+        self.s = torch.as_tensor(s, dtype=DT).reshape((self.lat.Q,) + self.shape).clone()
+
+    # ---- dynamics -----------------------------------------------------------------
+    def pre_collision(self):
+        return ST.pull(self.s, self.lat, self.bc, self.uw)
+
+    def step(self, n=1):
+        for _ in range(n):
+            g = self.pre_collision()
+            self.s = C.collide(g, self.F, self.lat, self.p, self.cs_eff)
+
+    # ---- diagnostics --------------------------------------------------------------
+    def moments(self):
+        """(rho, u) of the current pre-collision field (Eqs. densitycalculation, velocitycalculation)."""
+        return C.hydrodynamics(self.pre_collision(), self.F, self.lat, self.p)
+
+    def reduce(self):
+        """[sum rho, sum rho u_x, sum rho u_y, sum rho u_z, sum rho |u|^2 / 2] (paper silent)."""
+        rho, u = self.moments()
+        return [float(rho.sum()), float((rho * u[0]).sum()), float((rho * u[1]).sum()),
+                float((rho * u[2]).sum()), float((0.5 * rho * (u * u).sum(0)).sum())]
+
+
+def collide_cells(g, F, lattice, params, cs_eff=None):
+    """Collision of a batch of independent cells: g[Q, n], F[3, n] (no streaming)."""
+    lat = get_lattice(lattice) if isinstance(lattice, str) else lattice
+    return C.collide(g, F, lat, params, cs_eff)

@@ -1,0 +1,206 @@
+"""Oracle pins: source hierarchy, source populations, conservation, relaxation, literal form.
+
+Secs. 5-10 of the paper. Each pin compares the generic oracle against a route the paper
+prints independently (explicit formulas, velocity-space sources, element-wise update) or
+against an exact invariant.
+"""
+import pytest
+import torch
+
+from oracle import lattice as L, moments as M, collision as C, literal as LIT
+
+DT = torch.float64
+
+
+def _state(lat, n, seed, amp=0.05, famp=1e-2):
+    g = torch.Generator().manual_seed(seed)
+    rho = 1 + amp * torch.randn(n, generator=g, dtype=DT)
+    u = 0.1 * torch.randn(3, n, generator=g, dtype=DT)
+    F = famp * torch.randn(3, n, generator=g, dtype=DT)
+    if lat.d == 2:
+        u[2] = 0
+        F[2] = 0
+    feq = C.equilibrium(rho, u, torch.zeros_like(F), lat)
+    fb = feq * (1 + amp * torch.randn(feq.shape, generator=g, dtype=DT))
+    return fb, F
+
+
+def test_source_hierarchy_matches_printed_d2q9_expressions():
+    """sigma from the generic recursion vs the expanded Eq. centralmomentforcingtransformed."""
+    lat = L.D2Q9
+    fb, F = _state(lat, 128, 10)
+    rho, u = C.hydrodynamics(fb, F, lat)
+    kb = M.central_moments(fb, u, lat)
+    sig, _ = C.source_central(kb, rho, F, lat)
+    Fx, Fy = F[0], F[1]
+    kxx, kyy, kxy, kxxy, kxyy = kb[3], kb[4], kb[5], kb[6], kb[7]
+    ref = [torch.zeros_like(rho), Fx, Fy, torch.zeros_like(rho), torch.zeros_like(rho), torch.zeros_like(rho),
+           2 * Fx / rho * kxy + Fy / rho * kxx,
+           Fx / rho * kyy + 2 * Fy / rho * kxy,
+           2 * Fx / rho * kxyy + 2 * Fy / rho * kxxy + Fy ** 2 / rho ** 2 * kxx + Fx ** 2 / rho ** 2 * kyy
+           + 4 * Fx * Fy / rho ** 2 * kxy]
+    for j in range(9):
+        assert torch.allclose(sig[j], ref[j], atol=1e-17, rtol=1e-13), j
+
+
+@pytest.mark.parametrize("name", ["D2Q9", "D3Q27"])
+def test_source_populations_satisfy_exact_identity(name):
+    """Central moments of S (explicit sums) equal Eq. centralmomentforceexactidentity2 applied to
+    the central moments of f = fbar + S/2 (Eq. transformedcentralmoments)."""
+    lat = L.get(name)
+    fb, F = _state(lat, 64, 11)
+    rho, u = C.hydrodynamics(fb, F, lat)
+    S = C.source_populations(fb, F, lat)
+    f = fb + 0.5 * S
+    kap = M.central_moments(f, u, lat)
+    sig = M.central_moments(S, u, lat)
+    idx = {a: k for k, a in enumerate(lat.monomials)}
+    for a in lat.monomials:
+        ref = torch.zeros_like(rho)
+        for d in range(3):
+            if a[d]:
+                lo = list(a)
+                lo[d] -= 1
+                ref = ref + a[d] * F[d] / rho * kap[idx[tuple(lo)]]
+        assert torch.allclose(sig[idx[a]], ref, atol=1e-15, rtol=1e-12), a
+    # conserved moments of f: kappa_0 = rho, kappa_x = 0 (Sec. 7)
+    for d in range(lat.d):
+        e = [0, 0, 0]
+        e[d] = 1
+        assert kap[idx[tuple(e)]].abs().max().item() < 1e-15
+
+
+def test_d2q9_source_equals_printed_velocity_space_terms():
+    """Generic S = T(u)^-1 sigma vs Eqs. vsourceterms0-8 built from Eqs. sourceterm0-8."""
+    lat = L.D2Q9
+    for seed in (12, 13):
+        fb, F = _state(lat, 128, seed)
+        _, _, S_lit = LIT.collide_literal(fb, F, (1.0,) * 6)
+        S_gen = C.source_populations(fb, F, lat)
+        assert (S_lit - S_gen).abs().max().item() < 1e-17
+
+
+def test_d2q9_source_raw_moments_printed():
+    """Raw moments of S vs Eqs. rawmomentsourceterm0-8 (sigma'_yy read as 2 F_y u_y)."""
+    lat = L.D2Q9
+    fb, F = _state(lat, 64, 14)
+    rho, u = C.hydrodynamics(fb, F, lat)
+    S = C.source_populations(fb, F, lat)
+    r = M.raw_moments(S, lat)
+    kb = M.central_moments(fb, u, lat)
+    ux, uy, Fx, Fy = u[0], u[1], F[0], F[1]
+    kxx, kyy, kxy, kxxy, kxyy = kb[3], kb[4], kb[5], kb[6], kb[7]
+    ref = [torch.zeros_like(rho), Fx, Fy, 2 * Fx * ux, 2 * Fy * uy, Fx * uy + Fy * ux,
+           2 * Fx * (kxy / rho + ux * uy) + Fy * (kxx / rho + ux * ux),
+           Fx * (kyy / rho + uy * uy) + 2 * Fy * (kxy / rho + ux * uy),
+           2 * Fx * ux * (kyy / rho + uy * uy) + 2 * Fy * uy * (kxx / rho + ux * ux)
+           + 2 * Fx / rho * kxyy + 2 * Fy / rho * kxxy + Fx ** 2 / rho ** 2 * kyy + Fy ** 2 / rho ** 2 * kxx
+           + 4 * (Fx * uy / rho + Fy * ux / rho + Fx * Fy / rho ** 2) * kxy]
+    for j in range(9):
+        assert torch.allclose(r[j], ref[j], atol=1e-17, rtol=1e-12), j
+    # the printed sigma'_yy = 2 F_x u_y is not the raw moment (typo reading)
+    assert (r[4] - 2 * Fx * uy).abs().max().item() > 1e-4
+
+
+@pytest.mark.parametrize("name", ["D2Q9", "D3Q27"])
+def test_collision_conserves_mass_and_adds_force(name):
+    lat = L.get(name)
+    fb, F = _state(lat, 64, 15)
+    p = C.Params(tau=0.62, omega_bulk=1.1, omega3=1.3, omega4=0.8)
+    post = C.collide(fb, F, lat, p)
+    d = post - fb
+    assert d.sum(0).abs().max().item() < 1e-15
+    for ax in range(3):
+        mom = (d * lat.e[:, ax].to(DT).view(-1, 1)).sum(0)
+        assert torch.allclose(mom, F[ax], atol=1e-15, rtol=0)
+
+
+@pytest.mark.parametrize("name", ["D2Q9", "D3Q27"])
+def test_equilibrium_is_fixed_point_without_force(name):
+    lat = L.get(name)
+    g = torch.Generator().manual_seed(16)
+    rho = 1 + 0.05 * torch.randn(32, generator=g, dtype=DT)
+    u = 0.1 * torch.randn(3, 32, generator=g, dtype=DT)
+    if lat.d == 2:
+        u[2] = 0
+    F = torch.zeros(3, 32, dtype=DT)
+    feq = C.equilibrium(rho, u, F, lat)
+    post = C.collide(feq, F, lat, C.Params(tau=0.7, omega3=1.2, omega4=0.9))
+    assert (post - feq).abs().max().item() < 1e-15
+
+
+@pytest.mark.parametrize("name", ["D2Q9", "D3Q27"])
+def test_relaxation_rates_by_order(name):
+    """Post-collision central moments (explicit sums about the pre-collision u): trace with
+    omega_b, deviator and off-diagonals with omega_nu = 1/tau, orders 3 and >= 4 with omega3, omega4."""
+    lat = L.get(name)
+    fb, F = _state(lat, 64, 17, famp=0.0)
+    p = C.Params(tau=0.62, omega_bulk=1.1, omega3=1.3, omega4=0.8)
+    rho, u = C.hydrodynamics(fb, F, lat)
+    pre = M.central_moments(fb, u, lat)
+    post = M.central_moments(C.collide(fb, F, lat, p), u, lat)
+    idx = {a: k for k, a in enumerate(lat.monomials)}
+    wnu = 1 / p.tau
+    diag = [idx[tuple(2 if c == d else 0 for c in range(3))] for d in range(lat.d)]
+    tr_pre = sum(pre[k] for k in diag) - lat.d * rho / 3
+    tr_post = sum(post[k] for k in diag) - lat.d * rho / 3
+    assert torch.allclose(tr_post, (1 - p.omega_bulk) * tr_pre, atol=1e-15)
+    dev_pre = pre[diag[0]] - pre[diag[1]]
+    dev_post = post[diag[0]] - post[diag[1]]
+    assert torch.allclose(dev_post, (1 - wnu) * dev_pre, atol=1e-15)
+    for a in lat.monomials:
+        n = sum(a)
+        k = idx[a]
+        if n == 2 and max(a) == 1:
+            assert torch.allclose(post[k], (1 - wnu) * pre[k], atol=1e-15)
+        if n >= 3:
+            w = p.omega3 if n == 3 else p.omega4
+            ref = (1 - w) * pre[k] + w * (rho * (1 / 3) ** (n // 2) if all(x % 2 == 0 for x in a) else 0)
+            assert torch.allclose(post[k], ref, atol=1e-15), a
+
+
+def test_literal_equals_generic_without_force():
+    lat = L.D2Q9
+    fb, F = _state(lat, 128, 18)
+    F = torch.zeros_like(F)
+    for tau, w_b, w3, w4 in [(0.8, 0.0, 1.0, 1.0), (0.55, 1.4, 1.7, 0.6)]:
+        wnu = 1 / tau
+        p = C.Params(tau=tau, omega_bulk=w_b, omega3=w3, omega4=w4)
+        om = (w_b if w_b else wnu, wnu, wnu, w3, w3, w4)
+        post_l, _, _ = LIT.collide_literal(fb, F, om)
+        post_g = C.collide(fb, F, lat, p)
+        assert (post_l - post_g).abs().max().item() < 1e-15
+
+
+def test_literal_vs_generic_with_force_residual_structure():
+    """With F != 0 the printed g6-g8 differ from relaxing toward Eq. centralmomenttransformed by
+    exactly +omega3 sigma at third order and -omega4 (u_y sigma_xxy + u_x sigma_xyy) at fourth
+    order; orders <= 2 agree. This pins both forms and documents the reading."""
+    lat = L.D2Q9
+    fb, F = _state(lat, 256, 19)
+    p = C.Params(tau=0.7, omega3=1.3, omega4=0.9)
+    om = (1 / 0.7, 1 / 0.7, 1 / 0.7, 1.3, 1.3, 0.9)
+    post_l, _, _ = LIT.collide_literal(fb, F, om)
+    post_g = C.collide(fb, F, lat, p)
+    rho, u = C.hydrodynamics(fb, F, lat)
+    kl = M.central_moments(post_l, u, lat)
+    kg = M.central_moments(post_g, u, lat)
+    sig, _ = C.source_central(M.central_moments(fb, u, lat), rho, F, lat)
+    for j in range(6):
+        assert (kl[j] - kg[j]).abs().max().item() < 1e-15
+    assert torch.allclose(kl[6] - kg[6], 1.3 * sig[6], atol=1e-16, rtol=1e-10)
+    assert torch.allclose(kl[7] - kg[7], 1.3 * sig[7], atol=1e-16, rtol=1e-10)
+    assert torch.allclose(kl[8] - kg[8], -0.9 * (u[1] * sig[6] + u[0] * sig[7]), atol=1e-16, rtol=1e-10)
+
+
+def test_literal_collision_kernel_raw_moments():
+    """Raw moments of K g (Eq. collisionkernelmoment) from the element-wise update."""
+    lat = L.D2Q9
+    fb, F = _state(lat, 64, 20)
+    post, (g3, g4, g5, g6, g7, g8), S = LIT.collide_literal(fb, F, (1.2, 1.3, 1.3, 1.1, 0.9, 1.0))
+    Om = post - fb - S
+    r = M.raw_moments(Om, lat)
+    z = torch.zeros_like(g3)
+    ref = [z, z, z, 6 * g3 + 2 * g4, 6 * g3 - 2 * g4, 4 * g5, -4 * g6, -4 * g7, 8 * g3 + 4 * g8]
+    for j in range(9):
+        assert torch.allclose(r[j], ref[j], atol=1e-16, rtol=1e-12), j
