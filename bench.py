@@ -1,0 +1,427 @@
+"""Benchmark of the cascaded central-moment stream-and-collide step (one JSON line on rank 0).
+
+Workload (N=1): D3Q27 FP32 decaying Taylor-Green vortex on a 256^3 periodic box, u0 = 0.05,
+Re = 1600 (tau from Re and L/(2 pi)), no eddy viscosity. A step is one launch of the fused
+pull + collide + store kernel over all 16.8 M cells. The state (2 x 1.81 GB) is far larger
+than the 129 MB L2, so no flush is needed between steps.
+
+Also reported (same JSON line, "forms"): BF16 / FP16 storage of the same workload, the
+512^3 forced LES (Smagorinsky) in FP32 / BF16 / FP16, the 1024x256x256 BF16 wall-bounded LES
+channel, and the adjoint rollout on 128^3 when available.
+
+--impl reference times the FP64 CPU oracle (the only baseline: the paper has no code).
+Multi-GPU: the path is timed as independent replicas (one full workload per rank, "weak").
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+BYTES_PER_CELL = {("D3Q27", "f32"): 216, ("D3Q27", "bf16"): 108, ("D3Q27", "f16"): 108, ("D3Q27", "f64"): 432,
+                  ("D2Q9", "f64"): 144, ("D2Q9", "f32"): 72}
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC = os.path.join(ROOT, "profiles", "traffic.txt")
+FALLBACK_HBM = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256, help="edge of the Taylor-Green box")
+    ap.add_argument("--no-forms", action="store_true", help="skip the secondary forms")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--form-steps", type=int, default=40)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------------------
+# distributed plumbing (replicas)
+# ------------------------------------------------------------------------------------------
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+            if backend == "nccl":
+                torch.cuda.set_device(self.local)
+            dist.init_process_group(backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, v):
+        if not self.pg:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ------------------------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------------------------------
+# helpers
+# ------------------------------------------------------------------------------------------
+def peaks():
+    try:
+        with open(PEAKS) as fh:
+            return json.load(fh), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": FALLBACK_HBM}, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1202_6074_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(key):
+    """DRAM bytes per cell from the committed ncu summary, when the kernels are unchanged since."""
+    try:
+        rows = {}
+        with open(TRAFFIC) as fh:
+            for line in fh:
+                if line.strip() and not line.startswith("#"):
+                    k, v = line.split("=", 1)
+                    rows[k.strip()] = v.strip()
+        if rows.get("source_hash") != kernel_source_hash():
+            return None
+        v = rows.get(key)
+        return float(v) if v else None
+    except (OSError, ValueError):
+        return None
+
+
+def tgv_tau(n, u0=0.05, re=1600.0):
+    return 3.0 * u0 * (n / (2 * math.pi)) / re + 0.5
+
+
+def time_steps(solver, steps, warmup, dist, stream):
+    solver.step(warmup)
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    l0 = solver.launch_count
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    solver.step(steps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    return ms, solver.launch_count - l0
+
+
+# ------------------------------------------------------------------------------------------
+# forms
+# ------------------------------------------------------------------------------------------
+def run_tgv(cm, n, storage, steps, warmup, dist, clocks=None):
+    from paper_1202_6074_gb300 import workloads as W
+
+    stream = torch.cuda.current_stream()
+    s = cm.Solver(lattice="D3Q27", nx=n, ny=n, nz=n, storage=storage, tau=tgv_tau(n))
+    rho, u = W.taylor_green(n, n, n, u0=0.05, xp=torch, device="cuda")
+    s.init(rho, u)
+    del rho, u
+    if clocks:
+        clocks.start()
+    ms, launches = time_steps(s, steps, warmup, dist, stream)
+    ck = clocks.stop() if clocks else None
+    red = s.reduce()
+    s.close()
+    return ms, launches, ck, red
+
+
+def run_hit_les(cm, n, storage, steps, warmup, dist):
+    from paper_1202_6074_gb300 import workloads as W
+
+    s = cm.Solver(lattice="D3Q27", nx=n, ny=n, nz=n, storage=storage, tau=0.5005, smagorinsky_cs=0.1)
+    F = W.hit_forcing(n, n, n, seed=1, xp=torch, device="cuda")
+    s.set_force((0, 0, 0), F)
+    del F
+    s.init()
+    ms, launches = time_steps(s, steps, warmup, dist, torch.cuda.current_stream())
+    s.close()
+    return ms, launches
+
+
+def run_channel(cm, storage, steps, warmup, dist, nx=1024, ny=256, nz=256):
+    u_tau, h = 0.005, ny / 2
+    nu0 = u_tau * h / 180.0
+    s = cm.Solver(lattice="D3Q27", nx=nx, ny=ny, nz=nz, storage=storage, tau=3 * nu0 + 0.5, smagorinsky_cs=0.1,
+                  van_driest=(26.0, u_tau / nu0), bc=("periodic", "bounceback", "periodic"))
+    s.set_force((u_tau * u_tau / h, 0.0, 0.0))
+    # laminar-shape start scaled to the bulk speed, with seeded noise (device generator)
+    y = (torch.arange(ny, device="cuda", dtype=torch.float64) + 0.5).view(1, ny, 1)
+    shape = 6.0 * y * (ny - y) / ny ** 2
+    ub = 15.7 * u_tau
+    g = torch.Generator(device="cuda").manual_seed(5)
+    u = 0.05 * 1.5 * ub * torch.randn((3, nz, ny, nx), generator=g, device="cuda", dtype=torch.float64) * (shape / 1.5)
+    u[0] += ub * shape
+    s.init(None, u)
+    del u
+    ms, launches = time_steps(s, steps, warmup, dist, torch.cuda.current_stream())
+    s.close()
+    return ms, launches
+
+
+def e2e(cm, n, storage, steps):
+    """Whole job through the C ABI with host buffers: upload (rho, u) from pinned memory, init,
+    `steps` steps, download (rho, u) and the FP64 reductions; wall clock around all of it."""
+    from paper_1202_6074_gb300 import workloads as W
+
+    rho, u = W.taylor_green(n, n, n, u0=0.05, xp=torch, device="cuda")
+    rho_h = rho.cpu().pin_memory()
+    u_h = u.cpu().pin_memory()
+    del rho, u
+    rho_o = torch.empty_like(rho_h).pin_memory()
+    u_o = torch.empty_like(u_h).pin_memory()
+    s = cm.Solver(lattice="D3Q27", nx=n, ny=n, nz=n, storage=storage, tau=tgv_tau(n))
+    lib = s.lib
+    P = cm._ptr
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s._check(lib.cmlbm_init(s.h, P(rho_h), P(u_h), cm.HOST))
+    s.step(steps)
+    s._check(lib.cmlbm_moments(s.h, P(rho_o), P(u_o), cm.HOST))
+    red = s.reduce()
+    t1 = time.perf_counter()
+    s.close()
+    N = n ** 3
+    assert math.isfinite(red[0])
+    return {"value": N * steps / (t1 - t0) / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": 32 * N / steps,
+            "d2h_bytes_per_step": (32 * N + 40) / steps, "steps": steps}
+
+
+def cpu_baseline(n=40, steps=4):
+    """The FP64 oracle on a bounded sample of the workload: a Taylor-Green box of n^3."""
+    from oracle.solver import OracleSim
+    from oracle.collision import Params
+    from paper_1202_6074_gb300 import workloads as W
+
+    rho, u = W.taylor_green(n, n, n, u0=0.05)
+    o = OracleSim("D3Q27", n, n, n, Params(tau=tgv_tau(n)))
+    o.init(torch.tensor(rho), torch.tensor(u))
+    t0 = time.perf_counter()
+    o.step(steps)
+    t1 = time.perf_counter()
+    return {"value": n ** 3 * steps / (t1 - t0) / 1e6, "unit": "MLUPS", "cores": torch.get_num_threads(),
+            "kind": "oracle", "sample": f"D3Q27 FP64 Taylor-Green {n}^3 x {steps} steps (same flow, smaller box)",
+            "seconds": t1 - t0}
+
+
+# ------------------------------------------------------------------------------------------
+# arms
+# ------------------------------------------------------------------------------------------
+def reference_arm(args, dist):
+    """The oracle as it stands, timed on the host cores: each step = one oracle step on a 32^3
+    Taylor-Green sample of the 256^3 workload."""
+    if dist.rank != 0:
+        return
+    from oracle.solver import OracleSim
+    from oracle.collision import Params
+    from paper_1202_6074_gb300 import workloads as W
+
+    n = 32
+    rho, u = W.taylor_green(n, n, n, u0=0.05)
+    o = OracleSim("D3Q27", n, n, n, Params(tau=tgv_tau(args.n)))
+    o.init(torch.tensor(rho), torch.tensor(u))
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    t1 = time.perf_counter()
+    v = n ** 3 * args.steps / (t1 - t0) / 1e6
+    sample = f"D3Q27 FP64 Taylor-Green {n}^3 per step (sample of the {args.n}^3 workload)"
+    print(json.dumps({
+        "impl": "reference", "metric": "MLUPS", "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * (t1 - t0) / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"D3Q27 Taylor-Green {args.n}^3 periodic, u0=0.05, Re=1600 (oracle sample {n}^3)"},
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": torch.get_num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def our_arm(args, dist):
+    import __graft_entry__ as G
+
+    G.build()
+    from paper_1202_6074_gb300 import cmlbm as cm
+
+    torch.cuda.set_device(dist.local)
+    n = args.n
+    N = n ** 3
+    pk, pk_kind = peaks()
+    clocks = Clocks(dist.local)
+    ms, launches, ck, red = run_tgv(cm, n, "f32", args.steps, args.warmup, dist, clocks)
+    ms = dist.max(ms)
+    per_launch_s = ms / 1e3 / args.steps
+    value = dist.world * N * args.steps / (ms / 1e3) / 1e6
+    bpc = BYTES_PER_CELL[("D3Q27", "f32")]
+    achieved = bpc * N / per_launch_s / 1e9
+    traffic_pc = measured_traffic("k_step_d3q27_f32_periodic")
+    line = {
+        "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": dist.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"D3Q27 CM-LBM FP32 decaying Taylor-Green vortex {n}^3 periodic, u0=0.05, Re=1600, "
+                               f"no LES (tau={tgv_tau(n):.6f})",
+                   "cells": N, "l2": "state 2 x %.2f GB >> 129 MB L2, no flush" % (27 * 4 * N / 1e9),
+                   "parallelism": "replicas" if dist.world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / pk["hbm_gbs"], "peak_kind": pk_kind,
+                     "traffic": None if traffic_pc is None else traffic_pc * N,
+                     "algorithmic_bytes_per_cell": bpc, "kernel": "k_step<D3Q27,f32,periodic>"},
+        "clocks": ck,
+        "gpu_launches": int(launches),
+        "diagnostics": {"mass": red[0], "kinetic_energy": red[4]},
+    }
+    if dist.rank == 0:
+        torch.cuda.empty_cache()
+        line["e2e"] = e2e(cm, n, "f32", max(args.steps // 4, 10))
+        forms = {}
+        if not args.no_forms:
+            fs = args.form_steps
+            for st in ("bf16", "f16"):
+                m, l, _, _ = run_tgv(cm, n, st, fs, 3, Dist0())
+                sec = m / 1e3 / fs
+                forms[f"tgv{n}_{st}"] = {"MLUPS": N / sec / 1e6, "hbm_frac": BYTES_PER_CELL[("D3Q27", st)] * N / sec / 1e9
+                                         / pk["hbm_gbs"], "steps": fs}
+            nh = 512
+            for st in ("f32", "bf16", "f16"):
+                try:
+                    m, l = run_hit_les(cm, nh, st, fs, 3, Dist0())
+                    sec = m / 1e3 / fs
+                    bpc_f = BYTES_PER_CELL[("D3Q27", st)] + 12
+                    forms[f"hit{nh}_les_{st}"] = {"MLUPS": nh ** 3 / sec / 1e6, "hbm_frac": bpc_f * nh ** 3 / sec / 1e9
+                                                  / pk["hbm_gbs"], "bytes_per_cell": bpc_f, "steps": fs}
+                except Exception as e:  # noqa: BLE001
+                    forms[f"hit{nh}_les_{st}"] = {"error": str(e)[:200]}
+                torch.cuda.empty_cache()
+            try:
+                m, l = run_channel(cm, "bf16", fs, 3, Dist0())
+                sec = m / 1e3 / fs
+                nc = 1024 * 256 * 256
+                forms["channel1024x256x256_les_bf16"] = {"MLUPS": nc / sec / 1e6, "hbm_frac": 108 * nc / sec / 1e9
+                                                         / pk["hbm_gbs"], "steps": fs}
+            except Exception as e:  # noqa: BLE001
+                forms["channel1024x256x256_les_bf16"] = {"error": str(e)[:200]}
+            torch.cuda.empty_cache()
+            try:
+                from paper_1202_6074_gb300 import rollout
+
+                forms["adjoint128_f32"] = rollout.benchmark(cm, n=128, steps=100, segment=50)
+            except Exception as e:  # noqa: BLE001
+                forms["adjoint128_f32"] = {"error": str(e)[:200]}
+        line["forms"] = forms
+        if not args.no_cpu:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line))
+
+
+class Dist0:
+    """Rank-local timing for the secondary forms (no collective)."""
+
+    def barrier(self):
+        pass
+
+
+def main():
+    args = parse()
+    dist = Dist()
+    try:
+        if args.impl == "reference":
+            reference_arm(args, dist)
+        else:
+            our_arm(args, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * cmlbm -- cascaded central-moment lattice Boltzmann step with Galilean-invariant forcing,
+ * as a C ABI over hand-written CUDA kernels for sm_103a (one GPU per handle).
+ *
+ * Method: K.N. Premnath and S. Banerjee, "Inertial frame independent forcing for discrete
+ * velocity Boltzmann equation: implications for filtered turbulence simulation",
+ * arXiv:1202.6074. Section and equation names below are the paper's.
+ *
+ * One step of the library (cmlbm_step) is, for every cell x:
+ *   pull      g_i(x) = s_i(x - e_i)                    (standard streaming, Eq. cascadedstreaming1)
+ *   moments   rho = sum g, rho u = sum g e + F/2        (Eqs. densitycalculation, velocitycalculation)
+ *   central   kbar_a = sum g (e - u)^a                  (Sec. 6, transformed central moments)
+ *   source    sigma_a by the exact hierarchical identity (Eq. centralmomentforceexactidentity2 with
+ *             kappa = kbar + sigma/2, Eq. transformedcentralmoments)
+ *   relax     post_a = kbar_a + omega_a (kappa^M_a - sigma_a/2 - kbar_a) + sigma_a
+ *             (attractors Eq. centralmomenttransformed; procedure of Secs. 9-10)
+ *   back      populations with the post-collision central moments (exact inverse, Sec. 8)
+ *   store     s_i(x) <- post-collision population.
+ * D3Q27, the Smagorinsky eddy viscosity, the boundaries and the storage formats are not in
+ * the paper (it is written for D2Q9 and says the procedure extends to 3D, Secs. 2 and 13);
+ * the readings used are stated at each field below.
+ *
+ * Conventions
+ *   - Every function returns CMLBM_OK (0) or a negative CMLBM_ERR_* code; nothing throws.
+ *     cmlbm_last_error() gives a message for the last failure on a handle.
+ *   - Calls are asynchronous on the handle's stream, except cmlbm_reduce, cmlbm_create,
+ *     cmlbm_destroy and calls with CMLBM_HOST buffers, which synchronise the stream.
+ *   - Buffers passed in are owned by the caller and only borrowed for the call.
+ *   - Grid layout: cell (x, y, z) has linear index c = (z * ny + y) * nx + x; N = nx*ny*nz.
+ *     Vector fields are [3][N] (component-major). Populations are [Q][N] (direction-major).
+ *   - Direction order. D2Q9 (Sec. 2, Eq. velocityd2q9 with the order of the basis
+ *     columns): 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1).
+ *     D3Q27: i = 9*(ez+1) + 3*(ey+1) + (ex+1).
+ *   - Rest weights w_i are the products of the 1D weights (1/6, 2/3, 1/6).
+ *   - State format: s_i(x) holds the post-collision transformed population fbar of cell x
+ *     encoded as d = fbar / w_i - 1 in the storage type (deviation from the rest weight,
+ *     round-to-nearest-even on store). The library keeps two state buffers.
+ */
+#ifndef CMLBM_H
+#define CMLBM_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define CMLBM_API __attribute__((visibility("default")))
+#else
+#define CMLBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------ */
+#define CMLBM_OK 0
+#define CMLBM_ERR_INVALID (-1)      /* bad argument or configuration */
+#define CMLBM_ERR_NOMEM (-2)        /* device or host allocation failed */
+#define CMLBM_ERR_CUDA (-3)         /* a CUDA runtime call failed (message has the CUDA error) */
+#define CMLBM_ERR_UNSUPPORTED (-4)  /* valid but not implemented for this configuration */
+#define CMLBM_ERR_DIVERGED (-5)     /* a reduction found a non-finite value */
+
+/* ---- enumerations ------------------------------------------------------------------ */
+enum { CMLBM_D2Q9 = 0, CMLBM_D3Q27 = 1 };                          /* lattice */
+enum { CMLBM_F64 = 0, CMLBM_F32 = 1, CMLBM_BF16 = 2, CMLBM_F16 = 3 }; /* state storage */
+enum { CMLBM_PERIODIC = 0, CMLBM_BOUNCEBACK = 1 };                 /* per-axis boundary */
+enum { CMLBM_DEVICE = 0, CMLBM_HOST = 1 };                         /* where a buffer lives */
+enum { CMLBM_ATTRACTOR_MAXWELL = 0, CMLBM_ATTRACTOR_FACTORIZED = 1 };
+
+typedef struct cmlbm cmlbm_t;
+
+/*
+ * Configuration. Fill with cmlbm_config_default() and override.
+ *   lattice, nx, ny, nz   D2Q9 needs nz == 1. Each size >= 1, N * Q < 2^40.
+ *   storage               arithmetic is FP64 for CMLBM_F64 storage and FP32 otherwise.
+ *   bc[3]                 per axis (x, y, z). Bounce-back puts half-way walls outside the
+ *                         first and last cells of that axis (paper silent on boundaries):
+ *                         g_i(x) = s_ibar(x) + 2 w_i rho_w (e_i . u_w) / c_s^2, rho_w = 1, u_w the
+ *                         crossed wall's velocity (the mean of both walls on an edge link).
+ *   wall_velocity[a][s]   velocity of the wall on axis a, side s (0 = below index 0, 1 = above n-1).
+ *   tau                   shear relaxation time: omega_nu = 1/tau, nu = c_s^2 (tau - 1/2)
+ *                         (Sec. 9, text after Eq. collisionkernelg8). Must satisfy tau > 1/2.
+ *   omega_bulk            rate of the trace of the second-order central moments (omega_3 of
+ *                         the paper); 0 = follow the (effective) shear rate.
+ *   omega_3, omega_4      rates of the third-order and of the fourth- and higher-order central
+ *                         moments (0 < omega < 2, Sec. 9).
+ *   smagorinsky_cs        Smagorinsky constant C_s; 0 disables the eddy viscosity. Reading
+ *                         (paper silent on the model; frame invariance required by Sec. 1):
+ *                         Pi = kappa_ij - c_s^2 rho delta_ij from second-order central moments,
+ *                         Q = |Pi|, tau_eff = (tau + sqrt(tau^2 + 18 sqrt(2) C^2 Q / rho)) / 2.
+ *   van_driest_aplus      A+ of the damping C = C_s (1 - exp(-y+/A+)); 0 disables. Needs y walls.
+ *   van_driest_utau_over_nu  u_tau / nu_0 so that y+ = y_wall * u_tau / nu_0, y_wall = distance to
+ *                         the nearest y wall (j + 1/2 or ny - 1/2 - j).
+ *   attractor             CMLBM_ATTRACTOR_MAXWELL (Eq. centralmomenttransformed) or
+ *                         CMLBM_ATTRACTOR_FACTORIZED (Sec. 11, Eq. factorxxyyfinal).
+ *   reduced_compressibility  1 = momentum rho0 u = sum fbar e + F/2 (Sec. 10).
+ *   rho0                  reference density of the reduced-compressibility form.
+ *   stream                cudaStream_t to launch on; NULL = the legacy default stream.
+ *   device                CUDA device ordinal the handle lives on.
+ */
+typedef struct {
+    int lattice;
+    int nx, ny, nz;
+    int storage;
+    int bc[3];
+    double wall_velocity[3][2][3];
+    double tau;
+    double omega_bulk;
+    double omega_3;
+    double omega_4;
+    double smagorinsky_cs;
+    double van_driest_aplus;
+    double van_driest_utau_over_nu;
+    int attractor;
+    int reduced_compressibility;
+    double rho0;
+    void* stream;
+    int device;
+} cmlbm_config;
+
+/* Defaults: D3Q27, 32^3, FP32, periodic, tau = 0.8, omega_bulk = 0, omega_3 = omega_4 = 1,
+ * no eddy viscosity, Maxwellian attractor, rho0 = 1, default stream, device 0. */
+CMLBM_API int cmlbm_config_default(cmlbm_config* cfg);
+
+/* Validate cfg, allocate two state buffers of Q*N storage elements on cfg->device and
+ * initialise the rest state (rho = 1, u = 0, F = 0). *out receives the handle.
+ * Errors: CMLBM_ERR_INVALID (bad sizes, tau <= 1/2, D2Q9 with nz != 1, van Driest without
+ * y walls), CMLBM_ERR_NOMEM, CMLBM_ERR_CUDA. On error *out is NULL. */
+CMLBM_API int cmlbm_create(const cmlbm_config* cfg, cmlbm_t** out);
+
+/* Release all device memory of the handle. NULL-safe. Synchronises the handle's stream. */
+CMLBM_API void cmlbm_destroy(cmlbm_t* h);
+
+/* Message of the last failed call on h, or of the last failed cmlbm_create on this thread
+ * when h is NULL. The string lives until the next failing call. */
+CMLBM_API const char* cmlbm_last_error(const cmlbm_t* h);
+
+/* Replace the stream the handle launches on (cudaStream_t, NULL = default stream). */
+CMLBM_API int cmlbm_set_stream(cmlbm_t* h, void* stream);
+
+/* Set the body force (paper: F in Eqs. cascadedLBE1 - velocitycalculation). uniform[3] is
+ * added to every cell; field (FP64, [3][N], on `where`) replaces it when non-NULL and is
+ * copied into the handle in the arithmetic precision (FP64 or FP32). NULL uniform = 0. */
+CMLBM_API int cmlbm_set_force(cmlbm_t* h, const double uniform[3], const double* field, int where);
+
+/* Initialise the state so that the next pull returns fbar = f^M(rho, u) - S/2 with the
+ * current force, S evaluated at the Maxwellian moments (paper silent on initialisation;
+ * the special case noted under Eq. exactidentitycomponents). rho [N] and u [3][N] are FP64
+ * on `where`; rho NULL means 1, u NULL means 0. The step counter is reset. */
+CMLBM_API int cmlbm_init(cmlbm_t* h, const double* rho, const double* u, int where);
+
+/* Advance nsteps stream-and-collide steps (nsteps >= 0). */
+CMLBM_API int cmlbm_step(cmlbm_t* h, int nsteps);
+
+/* One step from the state buffer src into dst (device pointers, Q*N storage elements each,
+ * not the handle's own buffers, src != dst), with the handle's configuration and force.
+ * Used for checkpointed recomputation; the handle's own state is untouched. */
+CMLBM_API int cmlbm_step_buffers(cmlbm_t* h, const void* src, void* dst);
+
+/* Density [N] and velocity [3][N] (FP64) of the current pre-collision field (pull of the
+ * stored state): Eqs. densitycalculation and velocitycalculation (reduced-compressibility
+ * form: u = (sum fbar e + F/2) / rho0). Either pointer may be NULL. */
+CMLBM_API int cmlbm_moments(cmlbm_t* h, double* rho, double* u, int where);
+
+/* Same as cmlbm_moments for an arbitrary state buffer (device, handle layout). */
+CMLBM_API int cmlbm_moments_of(cmlbm_t* h, const void* state, double* rho, double* u);
+
+/* FP64 reductions of the current field: out = {sum rho, sum rho u_x, sum rho u_y,
+ * sum rho u_z, sum rho |u|^2 / 2} (host array, synchronous, deterministic order).
+ * Returns CMLBM_ERR_DIVERGED if any of them is not finite. */
+CMLBM_API int cmlbm_reduce(cmlbm_t* h, double out[5]);
+
+/* Bytes of one state buffer (Q * N * storage size). */
+CMLBM_API size_t cmlbm_state_bytes(const cmlbm_t* h);
+
+/* Copy the current state out of / into the handle (raw storage format, bytes must equal
+ * cmlbm_state_bytes). */
+CMLBM_API int cmlbm_get_state(cmlbm_t* h, void* dst, size_t bytes, int where);
+CMLBM_API int cmlbm_set_state(cmlbm_t* h, const void* src, size_t bytes, int where);
+
+/* ---- adjoint (reverse mode of cmlbm_step_buffers; paper silent) ---------------------- *
+ * Adjoint state lambda is [Q][N] in the arithmetic precision (FP64 for F64 storage, FP32
+ * otherwise) and holds dL/ds for the post-collision populations s (not the encoded d).
+ * dLdF is an FP64 [3][N] accumulator. Supported for F64 and F32 storage, Maxwellian
+ * attractor, standard compressibility, without eddy viscosity; else CMLBM_ERR_UNSUPPORTED. */
+
+/* Terminal adjoint of a loss on the velocity of state s_T: given dL/du ([3][N] FP64,
+ * device) and optionally dL/drho ([N], NULL = 0), writes lambda_T = dL/ds_T and adds the
+ * direct force term (u depends on F through F/2) into dLdF. */
+CMLBM_API int cmlbm_adjoint_terminal(cmlbm_t* h, const void* state, const double* dLdu, const double* dLdrho,
+                           void* lambda, double* dLdF);
+
+/* One step back: state is s_t (the input of the step s_t -> s_{t+1}), lambda_in = dL/ds_{t+1},
+ * lambda_out = dL/ds_t (must not alias lambda_in); adds (dC/dF)^T lambda_in into dLdF. */
+CMLBM_API int cmlbm_step_adjoint(cmlbm_t* h, const void* state, const void* lambda_in, void* lambda_out, double* dLdF);
+
+/* Kernel launches issued by the handle so far (for benchmark accounting). */
+CMLBM_API long long cmlbm_launch_count(const cmlbm_t* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CMLBM_H */

@@ -1,0 +1,282 @@
+"""Thin ctypes binding of libcmlbm.so (argument marshalling only).
+
+Every computation runs in the CUDA library; PyTorch supplies device memory (tensors) and
+the stream. Importing this module loads the library and raises if it has not been built:
+there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcmlbm.so")
+
+OK, ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_UNSUPPORTED, ERR_DIVERGED = 0, -1, -2, -3, -4, -5
+D2Q9, D3Q27 = 0, 1
+F64, F32, BF16, F16 = 0, 1, 2, 3
+PERIODIC, BOUNCEBACK = 0, 1
+DEVICE, HOST = 0, 1
+
+LATTICES = {"D2Q9": D2Q9, "D3Q27": D3Q27}
+STORAGES = {"f64": F64, "f32": F32, "bf16": BF16, "f16": F16}
+TORCH_STORAGE = {F64: torch.float64, F32: torch.float32, BF16: torch.bfloat16, F16: torch.float16}
+BCS = {"periodic": PERIODIC, "bounceback": BOUNCEBACK}
+
+# every symbol declared in include/cmlbm.h
+SYMBOLS = ["cmlbm_config_default", "cmlbm_create", "cmlbm_destroy", "cmlbm_last_error", "cmlbm_set_stream",
+           "cmlbm_set_force", "cmlbm_init", "cmlbm_step", "cmlbm_step_buffers", "cmlbm_moments",
+           "cmlbm_moments_of", "cmlbm_reduce", "cmlbm_state_bytes", "cmlbm_get_state", "cmlbm_set_state",
+           "cmlbm_adjoint_terminal", "cmlbm_step_adjoint", "cmlbm_launch_count"]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("lattice", ctypes.c_int),
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("storage", ctypes.c_int),
+        ("bc", ctypes.c_int * 3),
+        ("wall_velocity", ((ctypes.c_double * 3) * 2) * 3),
+        ("tau", ctypes.c_double),
+        ("omega_bulk", ctypes.c_double),
+        ("omega_3", ctypes.c_double),
+        ("omega_4", ctypes.c_double),
+        ("smagorinsky_cs", ctypes.c_double),
+        ("van_driest_aplus", ctypes.c_double),
+        ("van_driest_utau_over_nu", ctypes.c_double),
+        ("attractor", ctypes.c_int),
+        ("reduced_compressibility", ctypes.c_int),
+        ("rho0", ctypes.c_double),
+        ("stream", ctypes.c_void_p),
+        ("device", ctypes.c_int),
+    ]
+
+
+class CmlbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"cmlbm error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load():
+    """Load libcmlbm.so (raises when it is missing: the product has no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_1202_6074_gb300.build`")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D, V = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double), None
+    sig = {
+        "cmlbm_config_default": (I, [ctypes.POINTER(Config)]),
+        "cmlbm_create": (I, [ctypes.POINTER(Config), ctypes.POINTER(P)]),
+        "cmlbm_destroy": (V, [P]),
+        "cmlbm_last_error": (ctypes.c_char_p, [P]),
+        "cmlbm_set_stream": (I, [P, P]),
+        "cmlbm_set_force": (I, [P, D, P, I]),
+        "cmlbm_init": (I, [P, P, P, I]),
+        "cmlbm_step": (I, [P, I]),
+        "cmlbm_step_buffers": (I, [P, P, P]),
+        "cmlbm_moments": (I, [P, P, P, I]),
+        "cmlbm_moments_of": (I, [P, P, P, P]),
+        "cmlbm_reduce": (I, [P, D]),
+        "cmlbm_state_bytes": (ctypes.c_size_t, [P]),
+        "cmlbm_get_state": (I, [P, P, ctypes.c_size_t, I]),
+        "cmlbm_set_state": (I, [P, P, ctypes.c_size_t, I]),
+        "cmlbm_adjoint_terminal": (I, [P, P, P, P, P, P]),
+        "cmlbm_step_adjoint": (I, [P, P, P, P, P]),
+        "cmlbm_launch_count": (ctypes.c_longlong, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        return ctypes.c_void_p(t.data_ptr())
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data_as(ctypes.c_void_p)
+    raise TypeError(type(t))
+
+
+def _as_vec3(v):
+    arr = (ctypes.c_double * 3)()
+    for d in range(3):
+        arr[d] = float(v[d]) if v is not None else 0.0
+    return arr
+
+
+def make_config(lattice="D3Q27", nx=32, ny=32, nz=32, storage="f32", bc=("periodic",) * 3, wall_velocity=None,
+                tau=0.8, omega_bulk=0.0, omega_3=1.0, omega_4=1.0, smagorinsky_cs=0.0, van_driest=None,
+                attractor="maxwell", reduced_compressibility=False, rho0=1.0, device=0, stream=None):
+    lib = load()
+    c = Config()
+    lib.cmlbm_config_default(ctypes.byref(c))
+    c.lattice = LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
+    c.nx, c.ny, c.nz = int(nx), int(ny), int(nz)
+    c.storage = STORAGES[storage] if isinstance(storage, str) else int(storage)
+    for a in range(3):
+        c.bc[a] = BCS[bc[a]] if isinstance(bc[a], str) else int(bc[a])
+    if wall_velocity is not None:
+        for a in range(3):
+            for s in range(2):
+                for d in range(3):
+                    c.wall_velocity[a][s][d] = float(wall_velocity[a][s][d])
+    c.tau = float(tau)
+    c.omega_bulk = float(omega_bulk)
+    c.omega_3 = float(omega_3)
+    c.omega_4 = float(omega_4)
+    c.smagorinsky_cs = float(smagorinsky_cs)
+    if van_driest is not None:
+        c.van_driest_aplus, c.van_driest_utau_over_nu = float(van_driest[0]), float(van_driest[1])
+    c.attractor = {"maxwell": 0, "factorized": 1}[attractor] if isinstance(attractor, str) else int(attractor)
+    c.reduced_compressibility = int(bool(reduced_compressibility))
+    c.rho0 = float(rho0)
+    c.device = int(device)
+    c.stream = stream
+    return c
+
+
+class Solver:
+    """One lattice on one GPU (owns a cmlbm handle). Fields are torch tensors.
+
+    Device inputs are CUDA float64 tensors: rho [nz, ny, nx], u and F [3, nz, ny, nx].
+    Host inputs (numpy float64 arrays) are copied by the library itself.
+    """
+
+    def __init__(self, **kw):
+        self.lib = load()
+        if kw.get("stream") is None and torch.cuda.is_available():
+            kw["stream"] = ctypes.c_void_p(torch.cuda.current_stream(kw.get("device", 0)).cuda_stream)
+        self.cfg = make_config(**kw)
+        h = ctypes.c_void_p()
+        rc = self.lib.cmlbm_create(ctypes.byref(self.cfg), ctypes.byref(h))
+        if rc != OK:
+            raise CmlbmError(rc, self.lib.cmlbm_last_error(None).decode())
+        self.h = h
+        self.Q = 27 if self.cfg.lattice == D3Q27 else 9
+        self.shape = (self.cfg.nz, self.cfg.ny, self.cfg.nx)
+        self.N = self.cfg.nx * self.cfg.ny * self.cfg.nz
+        self.device = torch.device("cuda", self.cfg.device)
+        self.state_dtype = TORCH_STORAGE[self.cfg.storage]
+        self.real_dtype = torch.float64 if self.cfg.storage == F64 else torch.float32
+
+    # ---- plumbing ---------------------------------------------------------------------
+    def _check(self, rc):
+        if rc != OK:
+            raise CmlbmError(rc, self.lib.cmlbm_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.cmlbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream=None):
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._check(self.lib.cmlbm_set_stream(self.h, ctypes.c_void_p(s.cuda_stream)))
+
+    @property
+    def launch_count(self):
+        return int(self.lib.cmlbm_launch_count(self.h))
+
+    # ---- API --------------------------------------------------------------------------
+    def set_force(self, uniform=(0.0, 0.0, 0.0), field=None):
+        where = HOST if isinstance(field, np.ndarray) else DEVICE
+        if isinstance(field, np.ndarray):
+            field = np.ascontiguousarray(field, dtype=np.float64)
+        elif field is not None:
+            field = field.to(self.device, torch.float64).contiguous()
+        self._field_keepalive = field
+        self._check(self.lib.cmlbm_set_force(self.h, _as_vec3(uniform), _ptr(field), where))
+
+    def init(self, rho=None, u=None):
+        host = isinstance(rho, np.ndarray) or isinstance(u, np.ndarray)
+        if host:
+            rho = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64)
+            u = None if u is None else np.ascontiguousarray(u, dtype=np.float64)
+        else:
+            rho = None if rho is None else rho.to(self.device, torch.float64).contiguous()
+            u = None if u is None else u.to(self.device, torch.float64).contiguous()
+        self._check(self.lib.cmlbm_init(self.h, _ptr(rho), _ptr(u), HOST if host else DEVICE))
+        self._init_keepalive = (rho, u)
+
+    def step(self, n=1):
+        self._check(self.lib.cmlbm_step(self.h, int(n)))
+
+    def step_buffers(self, src, dst):
+        self._check(self.lib.cmlbm_step_buffers(self.h, _ptr(src), _ptr(dst)))
+
+    def moments(self, state=None, host=False):
+        """(rho [nz,ny,nx], u [3,nz,ny,nx]) as float64; CUDA tensors, or numpy when host=True."""
+        if host:
+            rho = np.empty(self.shape)
+            u = np.empty((3,) + self.shape)
+            self._check(self.lib.cmlbm_moments(self.h, _ptr(rho), _ptr(u), HOST))
+            return rho, u
+        rho = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        u = torch.empty((3,) + self.shape, dtype=torch.float64, device=self.device)
+        if state is None:
+            self._check(self.lib.cmlbm_moments(self.h, _ptr(rho), _ptr(u), DEVICE))
+        else:
+            self._check(self.lib.cmlbm_moments_of(self.h, _ptr(state), _ptr(rho), _ptr(u)))
+        return rho, u
+
+    def reduce(self):
+        out = (ctypes.c_double * 5)()
+        self._check(self.lib.cmlbm_reduce(self.h, out))
+        return [out[k] for k in range(5)]
+
+    @property
+    def state_bytes(self):
+        return int(self.lib.cmlbm_state_bytes(self.h))
+
+    def new_state(self):
+        return torch.empty((self.Q,) + self.shape, dtype=self.state_dtype, device=self.device)
+
+    def get_state(self, out=None):
+        out = self.new_state() if out is None else out
+        self._check(self.lib.cmlbm_get_state(self.h, _ptr(out), self.state_bytes, DEVICE))
+        return out
+
+    def set_state(self, s):
+        s = s.to(self.device, self.state_dtype).contiguous()
+        self._check(self.lib.cmlbm_set_state(self.h, _ptr(s), self.state_bytes, DEVICE))
+        torch.cuda.current_stream(self.device).synchronize()
+
+    # ---- adjoint ----------------------------------------------------------------------
+    def adjoint_terminal(self, state, dLdu, lam, dLdF, dLdrho=None):
+        self._check(self.lib.cmlbm_adjoint_terminal(self.h, _ptr(state), _ptr(dLdu), _ptr(dLdrho), _ptr(lam),
+                                                    _ptr(dLdF)))
+
+    def step_adjoint(self, state, lam_in, lam_out, dLdF):
+        self._check(self.lib.cmlbm_step_adjoint(self.h, _ptr(state), _ptr(lam_in), _ptr(lam_out), _ptr(dLdF)))
+
+
+def rest_weights(lattice):
+    """Rest weights in the library's direction order (products of the 1D weights 1/6, 2/3, 1/6)."""
+    w1 = {-1: 1.0 / 6.0, 0: 2.0 / 3.0, 1: 1.0 / 6.0}
+    return np.array([w1[ex] * w1[ey] * (w1[ez] if lattice == "D3Q27" else 1.0)
+                     for (ex, ey, ez) in velocities(lattice)])
+
+
+def velocities(lattice):
+    if lattice == "D2Q9":
+        return [(0, 0, 0), (1, 0, 0), (0, 1, 0), (-1, 0, 0), (0, -1, 0), (1, 1, 0), (-1, 1, 0), (-1, -1, 0),
+                (1, -1, 0)]
+    return [((i % 3) - 1, (i // 3) % 3 - 1, i // 9 - 1) for i in range(27)]

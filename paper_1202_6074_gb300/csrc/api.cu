@@ -1,0 +1,476 @@
+// C ABI of the cascaded central-moment step (declarations and documentation in include/cmlbm.h).
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/cmlbm.h"
+#include "cm_launch.h"
+
+struct cmlbm {
+    cmlbm_config cfg;
+    cm::Params p;
+    int D = 3;                 // 2 (D2Q9) or 3 (D3Q27)
+    int Q = 27;
+    size_t esize = 4;          // bytes per stored population
+    size_t rsize = 4;          // bytes per arithmetic value (adjoint, force)
+    void* buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    void* force = nullptr;     // [3][N] arithmetic type
+    double* part = nullptr;    // reduction partials [kReduceMaxBlocks * 5]
+    double* red = nullptr;     // reduction result [5]
+    double* stage = nullptr;   // [4][N] FP64 staging for host buffers (allocated on first use)
+    cudaStream_t st = nullptr;
+    long long launches = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int fail(cmlbm* h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+int cuda_fail(cmlbm* h, cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(h, CMLBM_ERR_CUDA, m);
+}
+
+// Switches to the handle's device for the duration of a call and restores the caller's.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { prev = -1; }
+        if (prev != dev) ok = (cudaSetDevice(dev) == cudaSuccess);
+    }
+    ~DeviceGuard() {
+        int now = -1;
+        if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
+    }
+};
+
+size_t storage_size(int s) {
+    switch (s) {
+        case CMLBM_F64: return 8;
+        case CMLBM_F32: return 4;
+        case CMLBM_BF16: return 2;
+        case CMLBM_F16: return 2;
+    }
+    return 0;
+}
+
+// Dispatch on (lattice, storage) to a launcher template.
+template <class Fn>
+cudaError_t dispatch(const cmlbm* h, Fn&& fn) {
+    if (h->D == 3) {
+        switch (h->cfg.storage) {
+            case CMLBM_F64: return fn(std::integral_constant<int, 3>{}, (double*)nullptr);
+            case CMLBM_F32: return fn(std::integral_constant<int, 3>{}, (float*)nullptr);
+            case CMLBM_BF16: return fn(std::integral_constant<int, 3>{}, (__nv_bfloat16*)nullptr);
+            case CMLBM_F16: return fn(std::integral_constant<int, 3>{}, (__half*)nullptr);
+        }
+    } else {
+        switch (h->cfg.storage) {
+            case CMLBM_F64: return fn(std::integral_constant<int, 2>{}, (double*)nullptr);
+            case CMLBM_F32: return fn(std::integral_constant<int, 2>{}, (float*)nullptr);
+            case CMLBM_BF16: return fn(std::integral_constant<int, 2>{}, (__nv_bfloat16*)nullptr);
+            case CMLBM_F16: return fn(std::integral_constant<int, 2>{}, (__half*)nullptr);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t do_step(cmlbm* h, const void* src, void* dst) {
+    ++h->launches;
+    return dispatch(h, [&](auto d, auto* s) {
+        using S = std::remove_pointer_t<decltype(s)>;
+        return cm::launch_step<decltype(d)::value, S>(src, dst, h->force, h->p, h->st);
+    });
+}
+
+cudaError_t do_moments(cmlbm* h, const void* src, double* rho, double* u) {
+    ++h->launches;
+    return dispatch(h, [&](auto d, auto* s) {
+        using S = std::remove_pointer_t<decltype(s)>;
+        return cm::launch_moments<decltype(d)::value, S>(src, h->force, h->p, rho, u, h->st);
+    });
+}
+
+int ensure_stage(cmlbm* h) {
+    if (h->stage) return CMLBM_OK;
+    cudaError_t e = cudaMalloc(&h->stage, sizeof(double) * 4 * (size_t)h->p.N);
+    if (e != cudaSuccess) {
+        h->stage = nullptr;
+        cudaGetLastError();
+        return fail(h, CMLBM_ERR_NOMEM, "cudaMalloc of the host staging buffer failed");
+    }
+    return CMLBM_OK;
+}
+
+bool valid_omega(double w) { return w > 0.0 && w < 2.0; }
+
+}  // namespace
+
+extern "C" {
+
+int cmlbm_config_default(cmlbm_config* c) {
+    if (!c) return CMLBM_ERR_INVALID;
+    std::memset(c, 0, sizeof(*c));
+    c->lattice = CMLBM_D3Q27;
+    c->nx = c->ny = c->nz = 32;
+    c->storage = CMLBM_F32;
+    c->tau = 0.8;
+    c->omega_3 = 1.0;
+    c->omega_4 = 1.0;
+    c->rho0 = 1.0;
+    return CMLBM_OK;
+}
+
+const char* cmlbm_last_error(const cmlbm_t* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int cmlbm_create(const cmlbm_config* cfg, cmlbm_t** out) {
+    if (!out) return fail(nullptr, CMLBM_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!cfg) return fail(nullptr, CMLBM_ERR_INVALID, "cfg is NULL");
+    const cmlbm_config& c = *cfg;
+    if (c.lattice != CMLBM_D2Q9 && c.lattice != CMLBM_D3Q27) return fail(nullptr, CMLBM_ERR_INVALID, "unknown lattice");
+    if (storage_size(c.storage) == 0) return fail(nullptr, CMLBM_ERR_INVALID, "unknown storage");
+    if (c.nx < 1 || c.ny < 1 || c.nz < 1) return fail(nullptr, CMLBM_ERR_INVALID, "grid sizes must be >= 1");
+    if (c.lattice == CMLBM_D2Q9 && c.nz != 1) return fail(nullptr, CMLBM_ERR_INVALID, "D2Q9 needs nz == 1");
+    const long long N = (long long)c.nx * c.ny * c.nz;
+    if (N >= (1LL << 31)) return fail(nullptr, CMLBM_ERR_INVALID, "nx*ny*nz must be < 2^31");
+    if (c.nz > 65535) return fail(nullptr, CMLBM_ERR_INVALID, "nz must be <= 65535");
+    if (c.ny > 65535) return fail(nullptr, CMLBM_ERR_INVALID, "ny must be <= 65535");
+    for (int a = 0; a < 3; ++a)
+        if (c.bc[a] != CMLBM_PERIODIC && c.bc[a] != CMLBM_BOUNCEBACK)
+            return fail(nullptr, CMLBM_ERR_INVALID, "bc must be CMLBM_PERIODIC or CMLBM_BOUNCEBACK");
+    if (!(c.tau > 0.5) || !std::isfinite(c.tau)) return fail(nullptr, CMLBM_ERR_INVALID, "tau must be > 1/2");
+    if (c.omega_bulk != 0.0 && !valid_omega(c.omega_bulk)) return fail(nullptr, CMLBM_ERR_INVALID, "omega_bulk must be 0 or in (0, 2)");
+    if (!valid_omega(c.omega_3) || !valid_omega(c.omega_4)) return fail(nullptr, CMLBM_ERR_INVALID, "omega_3 and omega_4 must be in (0, 2)");
+    if (!(c.smagorinsky_cs >= 0.0)) return fail(nullptr, CMLBM_ERR_INVALID, "smagorinsky_cs must be >= 0");
+    if (c.van_driest_aplus != 0.0) {
+        if (!(c.van_driest_aplus > 0.0) || !(c.van_driest_utau_over_nu > 0.0))
+            return fail(nullptr, CMLBM_ERR_INVALID, "van Driest needs A+ > 0 and u_tau/nu > 0");
+        if (c.bc[1] != CMLBM_BOUNCEBACK) return fail(nullptr, CMLBM_ERR_INVALID, "van Driest damping needs walls in y");
+        if (c.smagorinsky_cs <= 0.0) return fail(nullptr, CMLBM_ERR_INVALID, "van Driest damping needs smagorinsky_cs > 0");
+    }
+    if (c.attractor != CMLBM_ATTRACTOR_MAXWELL && c.attractor != CMLBM_ATTRACTOR_FACTORIZED)
+        return fail(nullptr, CMLBM_ERR_INVALID, "unknown attractor");
+    if (c.reduced_compressibility && !(c.rho0 > 0.0)) return fail(nullptr, CMLBM_ERR_INVALID, "rho0 must be > 0");
+
+    cmlbm* h = new (std::nothrow) cmlbm();
+    if (!h) return fail(nullptr, CMLBM_ERR_NOMEM, "host allocation failed");
+    h->cfg = c;
+    h->D = (c.lattice == CMLBM_D3Q27) ? 3 : 2;
+    h->Q = (h->D == 3) ? 27 : 9;
+    h->esize = storage_size(c.storage);
+    h->rsize = (c.storage == CMLBM_F64) ? 8 : 4;
+    h->st = (cudaStream_t)c.stream;
+    cm::Params& p = h->p;
+    std::memset(&p, 0, sizeof(p));
+    p.nx = c.nx;
+    p.ny = c.ny;
+    p.nz = c.nz;
+    p.N = N;
+    for (int a = 0; a < 3; ++a) p.bc[a] = c.bc[a];
+    std::memcpy(p.uw, c.wall_velocity, sizeof(p.uw));
+    p.tau0 = c.tau;
+    p.omega_bulk = c.omega_bulk;
+    p.omega3 = c.omega_3;
+    p.omega4 = c.omega_4;
+    p.cs = c.smagorinsky_cs;
+    p.les = c.smagorinsky_cs > 0.0;
+    p.vd = c.van_driest_aplus > 0.0;
+    p.vd_aplus = c.van_driest_aplus;
+    p.vd_utau_nu = c.van_driest_utau_over_nu;
+    p.attractor = c.attractor;
+    p.reduced = c.reduced_compressibility ? 1 : 0;
+    p.rho0 = c.reduced_compressibility ? c.rho0 : 1.0;
+
+    DeviceGuard g(c.device);
+    if (!g.ok) {
+        delete h;
+        return fail(nullptr, CMLBM_ERR_CUDA, "cudaSetDevice failed");
+    }
+    const size_t bytes = (size_t)h->Q * (size_t)N * h->esize;
+    for (int k = 0; k < 2; ++k) {
+        if (cudaMalloc(&h->buf[k], bytes) != cudaSuccess) {
+            cudaGetLastError();
+            cmlbm_destroy(h);
+            return fail(nullptr, CMLBM_ERR_NOMEM, "cudaMalloc of the state buffers failed");
+        }
+    }
+    if (cudaMalloc(&h->part, sizeof(double) * 5 * cm::kReduceMaxBlocks) != cudaSuccess ||
+        cudaMalloc(&h->red, sizeof(double) * 5) != cudaSuccess) {
+        cudaGetLastError();
+        cmlbm_destroy(h);
+        return fail(nullptr, CMLBM_ERR_NOMEM, "cudaMalloc of the reduction buffers failed");
+    }
+    int rc = cmlbm_init(h, nullptr, nullptr, CMLBM_DEVICE);
+    if (rc != CMLBM_OK) {
+        std::string m = h->err;
+        cmlbm_destroy(h);
+        return fail(nullptr, rc, m);
+    }
+    cudaError_t e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) {
+        cmlbm_destroy(h);
+        return cuda_fail(nullptr, e, "initialisation");
+    }
+    *out = h;
+    return CMLBM_OK;
+}
+
+void cmlbm_destroy(cmlbm_t* h) {
+    if (!h) return;
+    DeviceGuard g(h->cfg.device);
+    cudaStreamSynchronize(h->st);
+    cudaFree(h->buf[0]);
+    cudaFree(h->buf[1]);
+    cudaFree(h->force);
+    cudaFree(h->part);
+    cudaFree(h->red);
+    cudaFree(h->stage);
+    delete h;
+}
+
+int cmlbm_set_stream(cmlbm_t* h, void* stream) {
+    if (!h) return CMLBM_ERR_INVALID;
+    h->st = (cudaStream_t)stream;
+    return CMLBM_OK;
+}
+
+long long cmlbm_launch_count(const cmlbm_t* h) { return h ? h->launches : 0; }
+
+size_t cmlbm_state_bytes(const cmlbm_t* h) { return h ? (size_t)h->Q * (size_t)h->p.N * h->esize : 0; }
+
+int cmlbm_set_force(cmlbm_t* h, const double uniform[3], const double* field, int where) {
+    if (!h) return CMLBM_ERR_INVALID;
+    DeviceGuard g(h->cfg.device);
+    for (int d = 0; d < 3; ++d) {
+        const double v = uniform ? uniform[d] : 0.0;
+        if (!std::isfinite(v)) return fail(h, CMLBM_ERR_INVALID, "uniform force must be finite");
+        h->p.F[d] = v;
+    }
+    if (!field) {
+        h->p.has_field = 0;
+        return CMLBM_OK;
+    }
+    if (where != CMLBM_DEVICE && where != CMLBM_HOST) return fail(h, CMLBM_ERR_INVALID, "bad `where`");
+    const long long n = 3 * h->p.N;
+    if (!h->force) {
+        if (cudaMalloc(&h->force, h->rsize * (size_t)n) != cudaSuccess) {
+            h->force = nullptr;
+            cudaGetLastError();
+            return fail(h, CMLBM_ERR_NOMEM, "cudaMalloc of the force field failed");
+        }
+    }
+    const double* src = field;
+    if (where == CMLBM_HOST) {
+        int rc = ensure_stage(h);
+        if (rc) return rc;
+        cudaError_t e = cudaMemcpyAsync(h->stage, field, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, h->st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "force upload");
+        src = h->stage;
+    }
+    ++h->launches;
+    cudaError_t e = cm::launch_convert_force(src, h->force, n, h->cfg.storage == CMLBM_F64, h->st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "force conversion");
+    if (where == CMLBM_HOST) {
+        e = cudaStreamSynchronize(h->st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "force upload");
+    }
+    h->p.has_field = 1;
+    return CMLBM_OK;
+}
+
+int cmlbm_init(cmlbm_t* h, const double* rho, const double* u, int where) {
+    if (!h) return CMLBM_ERR_INVALID;
+    if (where != CMLBM_DEVICE && where != CMLBM_HOST) return fail(h, CMLBM_ERR_INVALID, "bad `where`");
+    DeviceGuard g(h->cfg.device);
+    const size_t N = (size_t)h->p.N;
+    const double* drho = rho;
+    const double* du = u;
+    if (where == CMLBM_HOST && (rho || u)) {
+        int rc = ensure_stage(h);
+        if (rc) return rc;
+        if (rho) {
+            cudaError_t e = cudaMemcpyAsync(h->stage, rho, sizeof(double) * N, cudaMemcpyHostToDevice, h->st);
+            if (e != cudaSuccess) return cuda_fail(h, e, "rho upload");
+            drho = h->stage;
+        }
+        if (u) {
+            cudaError_t e = cudaMemcpyAsync(h->stage + N, u, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, h->st);
+            if (e != cudaSuccess) return cuda_fail(h, e, "u upload");
+            du = h->stage + N;
+        }
+    }
+    void* tmp = h->buf[1 - h->cur];
+    void* dst = h->buf[h->cur];
+    h->launches += 2;
+    cudaError_t e = dispatch(h, [&](auto d, auto* s) {
+        using S = std::remove_pointer_t<decltype(s)>;
+        return cm::launch_init<decltype(d)::value, S>(tmp, dst, h->force, h->p, drho, du, h->st);
+    });
+    if (e != cudaSuccess) return cuda_fail(h, e, "init kernels");
+    if (where == CMLBM_HOST) {
+        e = cudaStreamSynchronize(h->st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "init");
+    }
+    return CMLBM_OK;
+}
+
+int cmlbm_step(cmlbm_t* h, int nsteps) {
+    if (!h) return CMLBM_ERR_INVALID;
+    if (nsteps < 0) return fail(h, CMLBM_ERR_INVALID, "nsteps must be >= 0");
+    DeviceGuard g(h->cfg.device);
+    for (int k = 0; k < nsteps; ++k) {
+        cudaError_t e = do_step(h, h->buf[h->cur], h->buf[1 - h->cur]);
+        if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
+        h->cur ^= 1;
+    }
+    return CMLBM_OK;
+}
+
+int cmlbm_step_buffers(cmlbm_t* h, const void* src, void* dst) {
+    if (!h) return CMLBM_ERR_INVALID;
+    if (!src || !dst || src == dst) return fail(h, CMLBM_ERR_INVALID, "src and dst must be distinct device buffers");
+    DeviceGuard g(h->cfg.device);
+    cudaError_t e = do_step(h, src, dst);
+    if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
+    return CMLBM_OK;
+}
+
+int cmlbm_moments_of(cmlbm_t* h, const void* state, double* rho, double* u) {
+    if (!h) return CMLBM_ERR_INVALID;
+    if (!state) return fail(h, CMLBM_ERR_INVALID, "state is NULL");
+    if (!rho && !u) return CMLBM_OK;
+    DeviceGuard g(h->cfg.device);
+    cudaError_t e = do_moments(h, state, rho, u);
+    if (e != cudaSuccess) return cuda_fail(h, e, "moments kernel");
+    return CMLBM_OK;
+}
+
+int cmlbm_moments(cmlbm_t* h, double* rho, double* u, int where) {
+    if (!h) return CMLBM_ERR_INVALID;
+    if (where != CMLBM_DEVICE && where != CMLBM_HOST) return fail(h, CMLBM_ERR_INVALID, "bad `where`");
+    if (!rho && !u) return CMLBM_OK;
+    DeviceGuard g(h->cfg.device);
+    if (where == CMLBM_DEVICE) return cmlbm_moments_of(h, h->buf[h->cur], rho, u);
+    int rc = ensure_stage(h);
+    if (rc) return rc;
+    const size_t N = (size_t)h->p.N;
+    cudaError_t e = do_moments(h, h->buf[h->cur], h->stage, h->stage + N);
+    if (e != cudaSuccess) return cuda_fail(h, e, "moments kernel");
+    if (rho && (e = cudaMemcpyAsync(rho, h->stage, sizeof(double) * N, cudaMemcpyDeviceToHost, h->st)) != cudaSuccess)
+        return cuda_fail(h, e, "rho download");
+    if (u && (e = cudaMemcpyAsync(u, h->stage + N, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, h->st)) != cudaSuccess)
+        return cuda_fail(h, e, "u download");
+    e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "moments");
+    return CMLBM_OK;
+}
+
+int cmlbm_reduce(cmlbm_t* h, double out[5]) {
+    if (!h || !out) return CMLBM_ERR_INVALID;
+    DeviceGuard g(h->cfg.device);
+    h->launches += 2;
+    cudaError_t e = dispatch(h, [&](auto d, auto* s) {
+        using S = std::remove_pointer_t<decltype(s)>;
+        return cm::launch_reduce<decltype(d)::value, S>(h->buf[h->cur], h->force, h->p, h->part, h->red, h->st);
+    });
+    if (e != cudaSuccess) return cuda_fail(h, e, "reduction kernels");
+    e = cudaMemcpyAsync(out, h->red, sizeof(double) * 5, cudaMemcpyDeviceToHost, h->st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "reduction download");
+    e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "reduction");
+    for (int k = 0; k < 5; ++k)
+        if (!std::isfinite(out[k])) return fail(h, CMLBM_ERR_DIVERGED, "non-finite value in the reductions");
+    return CMLBM_OK;
+}
+
+int cmlbm_get_state(cmlbm_t* h, void* dst, size_t bytes, int where) {
+    if (!h || !dst) return CMLBM_ERR_INVALID;
+    if (bytes != cmlbm_state_bytes(h)) return fail(h, CMLBM_ERR_INVALID, "bytes must equal cmlbm_state_bytes");
+    if (where != CMLBM_DEVICE && where != CMLBM_HOST) return fail(h, CMLBM_ERR_INVALID, "bad `where`");
+    DeviceGuard g(h->cfg.device);
+    cudaError_t e = cudaMemcpyAsync(dst, h->buf[h->cur], bytes, where == CMLBM_HOST ? cudaMemcpyDeviceToHost
+                                                                                   : cudaMemcpyDeviceToDevice, h->st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "state copy");
+    if (where == CMLBM_HOST && (e = cudaStreamSynchronize(h->st)) != cudaSuccess) return cuda_fail(h, e, "state copy");
+    return CMLBM_OK;
+}
+
+int cmlbm_set_state(cmlbm_t* h, const void* src, size_t bytes, int where) {
+    if (!h || !src) return CMLBM_ERR_INVALID;
+    if (bytes != cmlbm_state_bytes(h)) return fail(h, CMLBM_ERR_INVALID, "bytes must equal cmlbm_state_bytes");
+    if (where != CMLBM_DEVICE && where != CMLBM_HOST) return fail(h, CMLBM_ERR_INVALID, "bad `where`");
+    DeviceGuard g(h->cfg.device);
+    cudaError_t e = cudaMemcpyAsync(h->buf[h->cur], src, bytes, where == CMLBM_HOST ? cudaMemcpyHostToDevice
+                                                                                   : cudaMemcpyDeviceToDevice, h->st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "state copy");
+    if (where == CMLBM_HOST && (e = cudaStreamSynchronize(h->st)) != cudaSuccess) return cuda_fail(h, e, "state copy");
+    return CMLBM_OK;
+}
+
+static int adjoint_supported(cmlbm* h) {
+    if (h->cfg.storage != CMLBM_F64 && h->cfg.storage != CMLBM_F32)
+        return fail(h, CMLBM_ERR_UNSUPPORTED, "the adjoint needs F64 or F32 storage");
+    if (h->p.les || h->p.attractor != 0 || h->p.reduced)
+        return fail(h, CMLBM_ERR_UNSUPPORTED, "the adjoint supports the Maxwellian attractor without eddy viscosity");
+    return CMLBM_OK;
+}
+
+int cmlbm_adjoint_terminal(cmlbm_t* h, const void* state, const double* dLdu, const double* dLdrho, void* lambda,
+                           double* dLdF) {
+    if (!h) return CMLBM_ERR_INVALID;
+    if (!state || !dLdu || !lambda || !dLdF) return fail(h, CMLBM_ERR_INVALID, "NULL argument");
+    int rc = adjoint_supported(h);
+    if (rc) return rc;
+    DeviceGuard g(h->cfg.device);
+    ++h->launches;
+    cudaError_t e;
+    if (h->D == 3)
+        e = (h->cfg.storage == CMLBM_F64)
+                ? cm::launch_adjoint_terminal<3, double>(state, h->force, h->p, dLdu, dLdrho, lambda, dLdF, h->st)
+                : cm::launch_adjoint_terminal<3, float>(state, h->force, h->p, dLdu, dLdrho, lambda, dLdF, h->st);
+    else
+        e = (h->cfg.storage == CMLBM_F64)
+                ? cm::launch_adjoint_terminal<2, double>(state, h->force, h->p, dLdu, dLdrho, lambda, dLdF, h->st)
+                : cm::launch_adjoint_terminal<2, float>(state, h->force, h->p, dLdu, dLdrho, lambda, dLdF, h->st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "adjoint terminal kernel");
+    return CMLBM_OK;
+}
+
+int cmlbm_step_adjoint(cmlbm_t* h, const void* state, const void* lambda_in, void* lambda_out, double* dLdF) {
+    if (!h) return CMLBM_ERR_INVALID;
+    if (!state || !lambda_in || !lambda_out || !dLdF) return fail(h, CMLBM_ERR_INVALID, "NULL argument");
+    if (lambda_in == lambda_out) return fail(h, CMLBM_ERR_INVALID, "lambda_in and lambda_out must not alias");
+    int rc = adjoint_supported(h);
+    if (rc) return rc;
+    DeviceGuard g(h->cfg.device);
+    ++h->launches;
+    cudaError_t e;
+    if (h->D == 3)
+        e = (h->cfg.storage == CMLBM_F64)
+                ? cm::launch_adjoint_step<3, double>(state, h->force, h->p, lambda_in, lambda_out, dLdF, h->st)
+                : cm::launch_adjoint_step<3, float>(state, h->force, h->p, lambda_in, lambda_out, dLdF, h->st);
+    else
+        e = (h->cfg.storage == CMLBM_F64)
+                ? cm::launch_adjoint_step<2, double>(state, h->force, h->p, lambda_in, lambda_out, dLdF, h->st)
+                : cm::launch_adjoint_step<2, float>(state, h->force, h->p, lambda_in, lambda_out, dLdF, h->st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "adjoint step kernel");
+    return CMLBM_OK;
+}
+
+}  // extern "C"

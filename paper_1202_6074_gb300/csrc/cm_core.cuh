@@ -1,0 +1,431 @@
+// Device code of the cascaded central-moment step (arXiv:1202.6074) for sm_103a.
+//
+// Layout: populations are direction-major [Q][N] with N = nx*ny*nz, cell c = (z*ny + y)*nx + x.
+// A thread owns one cell and keeps its Q populations in registers in "tensor" order
+// t = (ex+1) + 3*(ey+1) + 9*(ez+1); after the forward axis sweeps the same slot holds the
+// central moment with exponents (alpha, beta, gamma) = (t%3, t/3%3, t/9).
+//
+// Arithmetic is carried on deviations from the rest state: h_i = fbar_i - w_i, and central
+// moments of h about u. The central moments of the weights about u are the products
+// prod_d c_{a_d}(u_d) with c_0 = 1, c_1 = -u, c_2 = 1/3 + u^2, so every quantity the kernel
+// rounds is O(u, drho, F) rather than O(1). The algebra is exact: it is the same step as the
+// paper's (Secs. 6-10) with the weights' moments moved out analytically.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace cm {
+
+// ------------------------------------------------------------------------------------------
+// Parameters (plain data, passed by value to every kernel)
+// ------------------------------------------------------------------------------------------
+struct Params {
+    int nx, ny, nz;
+    int bc[3];             // 0 periodic, 1 half-way bounce-back
+    int les;               // Smagorinsky eddy viscosity on
+    int vd;                // van Driest damping on (y walls)
+    int attractor;         // 0 Maxwellian, 1 factorized
+    int reduced;           // reduced compressibility (u = j / rho0)
+    int has_field;         // per-cell force field present
+    long long N;
+    double uw[3][2][3];    // wall velocities [axis][side][component]
+    double F[3];           // uniform force
+    double tau0;           // 1 / omega_nu (base)
+    double omega_bulk;     // 0 = follow the effective shear rate
+    double omega3, omega4;
+    double cs;             // Smagorinsky constant
+    double vd_aplus, vd_utau_nu;
+    double rho0;
+};
+
+// ------------------------------------------------------------------------------------------
+// Lattices
+// ------------------------------------------------------------------------------------------
+template <int D> struct Lat;
+
+template <> struct Lat<3> {
+    static constexpr int Q = 27;
+    static constexpr int NZ = 3;
+    __host__ __device__ static constexpr int ex(int i) { return i % 3 - 1; }
+    __host__ __device__ static constexpr int ey(int i) { return (i / 3) % 3 - 1; }
+    __host__ __device__ static constexpr int ez(int i) { return i / 9 - 1; }
+    __host__ __device__ static constexpr int opp(int i) { return 26 - i; }
+};
+
+// Paper's D2Q9 numbering (Sec. 2).
+template <> struct Lat<2> {
+    static constexpr int Q = 9;
+    static constexpr int NZ = 1;
+    __host__ __device__ static constexpr int ex(int i) {
+        return i == 1 ? 1 : i == 3 ? -1 : i == 5 ? 1 : i == 6 ? -1 : i == 7 ? -1 : i == 8 ? 1 : 0;
+    }
+    __host__ __device__ static constexpr int ey(int i) {
+        return i == 2 ? 1 : i == 4 ? -1 : i == 5 ? 1 : i == 6 ? 1 : i == 7 ? -1 : i == 8 ? -1 : 0;
+    }
+    __host__ __device__ static constexpr int ez(int) { return 0; }
+    __host__ __device__ static constexpr int opp(int i) {
+        return i == 0 ? 0 : i <= 4 ? ((i + 1) % 4 + 1) : ((i - 5 + 2) % 4 + 5);
+    }
+};
+
+template <int D> __host__ __device__ constexpr int slot(int i) {
+    return (Lat<D>::ex(i) + 1) + 3 * (Lat<D>::ey(i) + 1) + 9 * (Lat<D>::ez(i) + 1);
+}
+__host__ __device__ constexpr double w1(int e) { return e == 0 ? 2.0 / 3.0 : 1.0 / 6.0; }
+template <int D> __host__ __device__ constexpr double weight(int i) {
+    return w1(Lat<D>::ex(i)) * w1(Lat<D>::ey(i)) * (D == 3 ? w1(Lat<D>::ez(i)) : 1.0);
+}
+template <int D> __host__ __device__ constexpr double inv_weight(int i) { return 1.0 / weight<D>(i); }
+
+__host__ __device__ constexpr int ord(int t) { return t % 3 + (t / 3) % 3 + t / 9; }
+__host__ __device__ constexpr int ex_a(int t) { return t % 3; }
+__host__ __device__ constexpr int ex_b(int t) { return (t / 3) % 3; }
+__host__ __device__ constexpr int ex_c(int t) { return t / 9; }
+__host__ __device__ constexpr int midx(int a, int b, int c) { return a + 3 * b + 9 * c; }
+__host__ __device__ constexpr double third_pow(int n) { return n == 0 ? 1.0 : third_pow(n - 1) / 3.0; }
+
+// ------------------------------------------------------------------------------------------
+// Storage codec: d = fbar / w - 1 stored as S; arithmetic type R
+// ------------------------------------------------------------------------------------------
+template <class S> struct Codec;
+template <> struct Codec<double> {
+    using R = double;
+    static __device__ __forceinline__ R ld(const double* p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(double* p, R v) { *p = v; }
+};
+template <> struct Codec<float> {
+    using R = float;
+    static __device__ __forceinline__ R ld(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(float* p, R v) { *p = v; }
+};
+template <> struct Codec<__nv_bfloat16> {
+    using R = float;
+    static __device__ __forceinline__ R ld(const __nv_bfloat16* p) {
+        return __bfloat162float(__ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short*>(p))));
+    }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, R v) { *p = __float2bfloat16_rn(v); }
+};
+template <> struct Codec<__half> {
+    using R = float;
+    static __device__ __forceinline__ R ld(const __half* p) {
+        return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(p))));
+    }
+    static __device__ __forceinline__ void st(__half* p, R v) { *p = __float2half_rn(v); }
+};
+
+// ------------------------------------------------------------------------------------------
+// One-dimensional central-moment transforms on (e = -1, 0, +1) populations
+// ------------------------------------------------------------------------------------------
+// forward: (f-, f0, f+) -> (m0, m1, m2) with m_k = sum f (e - u)^k
+template <class R> __device__ __forceinline__ void fwd1(R& a, R& b, R& c, R u) {
+    R m0 = a + b + c;
+    R s1 = c - a;
+    R s2 = c + a;
+    R m1 = s1 - u * m0;
+    a = m0;
+    b = m1;
+    c = s2 - u * (s1 + m1);
+}
+// inverse: (m0, m1, m2) -> (f-, f0, f+)
+template <class R> __device__ __forceinline__ void inv1(R& a, R& b, R& c, R u) {
+    R m0 = a, m1 = b, m2 = c;
+    R r1 = m1 + u * m0;
+    R r2 = m2 + u * (m1 + r1);
+    a = R(0.5) * (r2 - r1);
+    b = m0 - r2;
+    c = R(0.5) * (r2 + r1);
+}
+
+// ------------------------------------------------------------------------------------------
+// Pull with periodic wrap and half-way bounce-back; fills h (deviation populations, slot order)
+// ------------------------------------------------------------------------------------------
+template <int D, class S, bool WALLS>
+__device__ __forceinline__ void gather(const S* __restrict__ src, int x, int y, int z, const Params& p,
+                                       typename Codec<S>::R (&h)[Lat<D>::Q]) {
+    using R = typename Codec<S>::R;
+    constexpr int Q = Lat<D>::Q;
+    const long long N = p.N;
+    int xs[3], ys[3], zs[3];
+    bool xo[3] = {false, false, false}, yo[3] = {false, false, false}, zo[3] = {false, false, false};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {          // slot k <-> e = k - 1, source coordinate = x - e
+        int sx = x + 1 - k, sy = y + 1 - k, sz = z + 1 - k;
+        if (sx < 0 || sx >= p.nx) {
+            if (!WALLS || p.bc[0] == 0) sx += (sx < 0) ? p.nx : -p.nx;
+            else { xo[k] = true; sx = x; }
+        }
+        if (sy < 0 || sy >= p.ny) {
+            if (!WALLS || p.bc[1] == 0) sy += (sy < 0) ? p.ny : -p.ny;
+            else { yo[k] = true; sy = y; }
+        }
+        if constexpr (D == 3) {
+            if (sz < 0 || sz >= p.nz) {
+                if (!WALLS || p.bc[2] == 0) sz += (sz < 0) ? p.nz : -p.nz;
+                else { zo[k] = true; sz = z; }
+            }
+        } else {
+            sz = 0;
+        }
+        xs[k] = sx;
+        ys[k] = sy;
+        zs[k] = sz;
+    }
+    const unsigned cell = (unsigned)((z * p.ny + y) * p.nx + x);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int a = Lat<D>::ex(i) + 1, b = Lat<D>::ey(i) + 1, c = Lat<D>::ez(i) + 1;
+        R d;
+        if (WALLS && (xo[a] || yo[b] || zo[c])) {
+            d = Codec<S>::ld(src + (long long)Lat<D>::opp(i) * N + cell);
+            R wx = 0, wy = 0, wz = 0, cnt = 0;
+            // slot 2 (e = +1) crosses the lower wall (side 0), slot 0 (e = -1) the upper (side 1)
+            if (xo[a]) { const int s = (a == 2) ? 0 : 1; wx += (R)p.uw[0][s][0]; wy += (R)p.uw[0][s][1]; wz += (R)p.uw[0][s][2]; cnt += 1; }
+            if (yo[b]) { const int s = (b == 2) ? 0 : 1; wx += (R)p.uw[1][s][0]; wy += (R)p.uw[1][s][1]; wz += (R)p.uw[1][s][2]; cnt += 1; }
+            if (zo[c]) { const int s = (c == 2) ? 0 : 1; wx += (R)p.uw[2][s][0]; wy += (R)p.uw[2][s][1]; wz += (R)p.uw[2][s][2]; cnt += 1; }
+            const R eu = (R)Lat<D>::ex(i) * wx + (R)Lat<D>::ey(i) * wy + (R)Lat<D>::ez(i) * wz;
+            d += R(6) * eu / cnt;
+        } else {
+            const unsigned sc = (unsigned)((zs[c] * p.ny + ys[b]) * p.nx + xs[a]);
+            d = Codec<S>::ld(src + (long long)i * N + sc);
+        }
+        h[slot<D>(i)] = d * (R)weight<D>(i);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Hydrodynamic fields from deviation populations (Eqs. densitycalculation, velocitycalculation)
+// ------------------------------------------------------------------------------------------
+template <int D, class R> struct Hydro {
+    R drho, jx, jy, jz, ux, uy, uz;
+};
+
+template <int D, class R>
+__device__ __forceinline__ Hydro<D, R> hydro(const R (&h)[Lat<D>::Q], const R F[3], const Params& p) {
+    constexpr int NL = Lat<D>::Q / 3;
+    Hydro<D, R> o;
+    R drho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+        const R s0 = h[3 * l] + h[3 * l + 1] + h[3 * l + 2];
+        drho += s0;
+        jx += h[3 * l + 2] - h[3 * l];
+        const int b = l % 3, c = l / 3;
+        if (b == 2) jy += s0;
+        if (b == 0) jy -= s0;
+        if constexpr (D == 3) {
+            if (c == 2) jz += s0;
+            if (c == 0) jz -= s0;
+        }
+    }
+    o.drho = drho;
+    o.jx = jx + R(0.5) * F[0];
+    o.jy = jy + R(0.5) * F[1];
+    o.jz = jz + R(0.5) * F[2];
+    const R inv = R(1) / (p.reduced ? (R)p.rho0 : R(1) + drho);
+    o.ux = o.jx * inv;
+    o.uy = o.jy * inv;
+    o.uz = (D == 3) ? o.jz * inv : R(0);
+    return o;
+}
+
+// Forward sweeps: deviation populations (slot order) -> central moments of h about u.
+template <int D, class R>
+__device__ __forceinline__ void central_forward(R (&m)[Lat<D>::Q], R ux, R uy, R uz) {
+    constexpr int NL = Lat<D>::Q / 3;
+#pragma unroll
+    for (int l = 0; l < NL; ++l) fwd1(m[3 * l], m[3 * l + 1], m[3 * l + 2], ux);
+#pragma unroll
+    for (int c = 0; c < Lat<D>::NZ; ++c)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) fwd1(m[9 * c + a], m[9 * c + 3 + a], m[9 * c + 6 + a], uy);
+    if constexpr (D == 3) {
+#pragma unroll
+        for (int t = 0; t < 9; ++t) fwd1(m[t], m[9 + t], m[18 + t], uz);
+    }
+}
+
+// Inverse sweeps: central moments about u -> populations (slot order).
+template <int D, class R>
+__device__ __forceinline__ void central_inverse(R (&m)[Lat<D>::Q], R ux, R uy, R uz) {
+    constexpr int NL = Lat<D>::Q / 3;
+    if constexpr (D == 3) {
+#pragma unroll
+        for (int t = 0; t < 9; ++t) inv1(m[t], m[9 + t], m[18 + t], uz);
+    }
+#pragma unroll
+    for (int c = 0; c < Lat<D>::NZ; ++c)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) inv1(m[9 * c + a], m[9 * c + 3 + a], m[9 * c + 6 + a], uy);
+#pragma unroll
+    for (int l = 0; l < NL; ++l) inv1(m[3 * l], m[3 * l + 1], m[3 * l + 2], ux);
+}
+
+// prod_{d in S}(1/3 + q_d) - 3^{-|S|} without cancellation (all terms are non-negative)
+template <class R> __device__ __forceinline__ R excess(const R* q, bool x, bool y, bool z) {
+    R A = 0, tk = 1;
+    if (x) { A = (R(1) / 3 + q[0]) * A + q[0] * tk; tk *= R(1) / 3; }
+    if (y) { A = (R(1) / 3 + q[1]) * A + q[1] * tk; tk *= R(1) / 3; }
+    if (z) { A = (R(1) / 3 + q[2]) * A + q[2] * tk; tk *= R(1) / 3; }
+    return A;
+}
+
+// ------------------------------------------------------------------------------------------
+// The collision in central-moment space (generic form; see the file header and cmlbm.h).
+// In: h deviation populations (slot order), force F, the eddy-viscosity constant cs_eff (0 = off).
+// Out: h holds the post-collision deviation populations.
+// ------------------------------------------------------------------------------------------
+template <int D, class R>
+__device__ __forceinline__ void collide(R (&m)[Lat<D>::Q], const R F[3], const Params& p, R cs_eff) {
+    constexpr int Q = Lat<D>::Q;
+    const Hydro<D, R> hy = hydro<D, R>(m, F, p);
+    const R drho = hy.drho, rho = R(1) + hy.drho;
+    const R u[3] = {hy.ux, hy.uy, hy.uz};
+    central_forward<D, R>(m, u[0], u[1], u[2]);
+
+    const R q[3] = {u[0] * u[0], u[1] * u[1], u[2] * u[2]};
+    const R cw[3][3] = {{R(1), -u[0], R(1) / 3 + q[0]},
+                        {R(1), -u[1], R(1) / 3 + q[1]},
+                        {R(1), -u[2], R(1) / 3 + q[2]}};
+    const R irho = R(1) / rho;
+    const R Fr[3] = {F[0] * irho, F[1] * irho, F[2] * irho};
+    const R third = R(1) / 3;
+
+    // second order: non-equilibrium stress Pi = kappa - c_s^2 rho delta (kappa = kbar at order 2)
+    const R Pxx = m[midx(2, 0, 0)] + q[0] - drho * third;
+    const R Pyy = m[midx(0, 2, 0)] + q[1] - drho * third;
+    const R Pxy = m[midx(1, 1, 0)] + u[0] * u[1];
+    R Pzz = R(0), Pxz = R(0), Pyz = R(0);
+    if constexpr (D == 3) {
+        Pzz = m[midx(0, 0, 2)] + q[2] - drho * third;
+        Pxz = m[midx(1, 0, 1)] + u[0] * u[2];
+        Pyz = m[midx(0, 1, 1)] + u[1] * u[2];
+    }
+
+    R tau = (R)p.tau0;
+    if (cs_eff > R(0)) {
+        const R Qn = sqrt(Pxx * Pxx + Pyy * Pyy + Pzz * Pzz + R(2) * (Pxy * Pxy + Pxz * Pxz + Pyz * Pyz));
+        tau = R(0.5) * (tau + sqrt(tau * tau + R(25.455844122715710878) * cs_eff * cs_eff * Qn * irho));
+    }
+    const R wnu = R(1) / tau;
+    const R wb = (p.omega_bulk > 0.0) ? (R)p.omega_bulk : wnu;
+
+    // kappa of f at second order, used by the source recursion (sigma = 0 at second order)
+    R kap[Q];
+    kap[midx(2, 0, 0)] = Pxx + rho * third;
+    kap[midx(0, 2, 0)] = Pyy + rho * third;
+    kap[midx(1, 1, 0)] = Pxy;
+    if constexpr (D == 3) {
+        kap[midx(0, 0, 2)] = Pzz + rho * third;
+        kap[midx(1, 0, 1)] = Pxz;
+        kap[midx(0, 1, 1)] = Pyz;
+    }
+
+    // relaxed second order: trace with omega_b, deviator and off-diagonal with omega_nu
+    const R tr = Pxx + Pyy + Pzz;
+    const R corr = (wnu - wb) * tr * (R(1) / D);
+    const R Txx = (R(1) - wnu) * Pxx + corr;
+    const R Tyy = (R(1) - wnu) * Pyy + corr;
+    const R Tzz = (R(1) - wnu) * Pzz + corr;
+    const R Txy = (R(1) - wnu) * Pxy;
+    const R Txz = (R(1) - wnu) * Pxz;
+    const R Tyz = (R(1) - wnu) * Pyz;
+    const R Tdiag[3] = {Txx, Tyy, Tzz};
+    const R w3 = (R)p.omega3, w4 = (R)p.omega4;
+
+    // orders >= 3: source by the hierarchical identity, attractor, relaxation
+#pragma unroll
+    for (int n = 3; n <= 2 * D; ++n) {
+#pragma unroll
+        for (int t = 0; t < Q; ++t) {
+            if (ord(t) != n) continue;
+            const int a = ex_a(t), b = ex_b(t), c = ex_c(t);
+            R s = 0;
+            if (a > 0) s += R(a) * Fr[0] * kap[t > 0 ? t - 1 : 0];
+            if (b > 0) s += R(b) * Fr[1] * kap[t > 2 ? t - 3 : 0];
+            if (c > 0) s += R(c) * Fr[2] * kap[t > 8 ? t - 9 : 0];
+            const R kw = cw[0][a] * cw[1][b] * cw[2][c];
+            if (n < 2 * D) kap[t] = m[t] + kw + R(0.5) * s;
+            const bool even = (a % 2 == 0) && (b % 2 == 0) && (c % 2 == 0);
+            const int twos = (a == 2) + (b == 2) + (c == 2);
+            R DM;
+            if (p.attractor == 0) {
+                DM = even ? drho * (R)third_pow(twos) - excess(q, a == 2, b == 2, c == 2) : -kw;
+            } else {
+                // factorized attractor (Sec. 11): products of relaxed second-order moments / rho^(k-1)
+                const int ones = (a == 1) + (b == 1) + (c == 1);
+                if (ones == 0) {
+                    const R pt[3] = {Txx * irho, Tyy * irho, Tzz * irho};
+                    const R Ap = excess(pt, a == 2, b == 2, c == 2);
+                    const R Aq = excess(q, a == 2, b == 2, c == 2);
+                    R prodp = 1;
+                    if (a == 2) prodp *= third + pt[0];
+                    if (b == 2) prodp *= third + pt[1];
+                    if (c == 2) prodp *= third + pt[2];
+                    DM = drho * prodp + (Ap - Aq);
+                } else if (ones == 2 && twos == 1) {
+                    const int dtwo = (a == 2) ? 0 : (b == 2) ? 1 : 2;
+                    const R Toff = (a != 1) ? Tyz : (b != 1) ? Txz : Txy;
+                    const R uoff = (a != 1) ? u[1] * u[2] : (b != 1) ? u[0] * u[2] : u[0] * u[1];
+                    DM = Toff * (third + Tdiag[dtwo] * irho) - (third + q[dtwo]) * uoff;
+                } else {
+                    DM = -kw;
+                }
+            }
+            const R w = (n == 3) ? w3 : w4;
+            m[t] = (R(1) - w) * (m[t] + R(0.5) * s) + w * DM + R(0.5) * s;
+        }
+    }
+
+    // second order back to deviations of the weights' moments
+    m[midx(2, 0, 0)] = Txx + drho * third - q[0];
+    m[midx(0, 2, 0)] = Tyy + drho * third - q[1];
+    m[midx(1, 1, 0)] = Txy - u[0] * u[1];
+    if constexpr (D == 3) {
+        m[midx(0, 0, 2)] = Tzz + drho * third - q[2];
+        m[midx(1, 0, 1)] = Txz - u[0] * u[2];
+        m[midx(0, 1, 1)] = Tyz - u[1] * u[2];
+    }
+    // first order: collision invariant plus the source sigma_x = F_x
+    m[midx(1, 0, 0)] = hy.jx + R(0.5) * F[0] - drho * u[0];
+    m[midx(0, 1, 0)] = hy.jy + R(0.5) * F[1] - drho * u[1];
+    if constexpr (D == 3) m[midx(0, 0, 1)] = hy.jz + R(0.5) * F[2] - drho * u[2];
+    // zeroth order unchanged (m[0] = drho)
+
+    central_inverse<D, R>(m, u[0], u[1], u[2]);
+}
+
+// Equilibrium deviations fbar - w for (rho, u, F): central moments kappa^M - sigma^M / 2 about u
+template <int D, class R>
+__device__ __forceinline__ void equilibrium(R (&m)[Lat<D>::Q], R rho, R ux, R uy, R uz, const R F[3]) {
+    constexpr int Q = Lat<D>::Q;
+    const R u[3] = {ux, uy, uz};
+    const R q[3] = {ux * ux, uy * uy, uz * uz};
+    const R cw[3][3] = {{R(1), -u[0], R(1) / 3 + q[0]},
+                        {R(1), -u[1], R(1) / 3 + q[1]},
+                        {R(1), -u[2], R(1) / 3 + q[2]}};
+    const R drho = rho - R(1);
+    const R irho = R(1) / rho;
+#pragma unroll
+    for (int t = 0; t < Q; ++t) {
+        const int a = ex_a(t), b = ex_b(t), c = ex_c(t);
+        const int n = ord(t);
+        const bool even = (a % 2 == 0) && (b % 2 == 0) && (c % 2 == 0);
+        const int twos = (a == 2) + (b == 2) + (c == 2);
+        // sigma^M by the identity on the Maxwellian moments: non-zero only for one odd axis
+        R s = 0;
+        if (a == 1 && (b % 2 == 0) && (c % 2 == 0)) s += F[0] * irho * rho * (R)third_pow(twos);
+        if (b == 1 && (a % 2 == 0) && (c % 2 == 0)) s += F[1] * irho * rho * (R)third_pow(twos);
+        if (c == 1 && (a % 2 == 0) && (b % 2 == 0)) s += F[2] * irho * rho * (R)third_pow(twos);
+        const R kw = cw[0][a] * cw[1][b] * cw[2][c];
+        R DM;
+        if (n == 0) DM = drho;
+        else DM = even ? drho * (R)third_pow(twos) - excess(q, a == 2, b == 2, c == 2) : -kw;
+        m[t] = DM - R(0.5) * s;
+    }
+    central_inverse<D, R>(m, u[0], u[1], u[2]);
+}
+
+}  // namespace cm

@@ -1,0 +1,313 @@
+// Kernels and host launch templates, instantiated per (lattice, storage) in inst_*.cu.
+#pragma once
+
+#include "cm_core.cuh"
+
+namespace cm {
+
+// Threads per block of the cell kernels and the block shape for a given nx.
+constexpr int kBlock = 128;
+inline dim3 cell_block(int nx) {
+    int bx = 32;
+    while (bx < kBlock && bx < nx) bx *= 2;
+    return dim3(bx, kBlock / bx, 1);
+}
+inline dim3 cell_grid(const Params& p, dim3 b) {
+    return dim3((p.nx + b.x - 1) / b.x, (p.ny + b.y - 1) / b.y, p.nz);
+}
+
+template <class R>
+__device__ __forceinline__ void load_force(const R* __restrict__ Ff, const Params& p, unsigned cell, R F[3]) {
+    if (p.has_field) {
+        F[0] = __ldg(Ff + cell);
+        F[1] = __ldg(Ff + p.N + cell);
+        F[2] = __ldg(Ff + 2 * p.N + cell);
+    } else {
+        F[0] = (R)p.F[0];
+        F[1] = (R)p.F[1];
+        F[2] = (R)p.F[2];
+    }
+}
+
+template <class R>
+__device__ __forceinline__ R smagorinsky_constant(const Params& p, int y) {
+    if (!p.les) return R(0);
+    R c = (R)p.cs;
+    if (p.vd) {
+        const R yw = fmin((R)y + R(0.5), (R)p.ny - R(0.5) - (R)y);
+        c *= R(1) - exp(-yw * (R)p.vd_utau_nu / (R)p.vd_aplus);
+    }
+    return c;
+}
+
+// ---- fused pull + collide + store --------------------------------------------------------
+template <int D, class S, bool WALLS>
+__global__ void __launch_bounds__(kBlock) k_step(const S* __restrict__ src, S* __restrict__ dst,
+                                                const typename Codec<S>::R* __restrict__ Ff, Params p) {
+    using R = typename Codec<S>::R;
+    constexpr int Q = Lat<D>::Q;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= p.nx || y >= p.ny) return;
+    const unsigned cell = (unsigned)((z * p.ny + y) * p.nx + x);
+    R h[Q];
+    gather<D, S, WALLS>(src, x, y, z, p, h);
+    R F[3];
+    load_force<R>(Ff, p, cell, F);
+    collide<D, R>(h, F, p, smagorinsky_constant<R>(p, y));
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        Codec<S>::st(dst + (long long)i * p.N + cell, h[slot<D>(i)] * (R)inv_weight<D>(i));
+}
+
+// ---- density and velocity of the pulled field ----------------------------------------------
+template <int D, class S, bool WALLS>
+__global__ void __launch_bounds__(kBlock) k_moments(const S* __restrict__ src, const typename Codec<S>::R* __restrict__ Ff,
+                                                   Params p, double* __restrict__ rho, double* __restrict__ u) {
+    using R = typename Codec<S>::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= p.nx || y >= p.ny) return;
+    const unsigned cell = (unsigned)((z * p.ny + y) * p.nx + x);
+    R h[Lat<D>::Q];
+    gather<D, S, WALLS>(src, x, y, z, p, h);
+    R F[3];
+    load_force<R>(Ff, p, cell, F);
+    const Hydro<D, R> hy = hydro<D, R>(h, F, p);
+    if (rho) rho[cell] = 1.0 + (double)hy.drho;
+    if (u) {
+        u[cell] = (double)hy.ux;
+        u[p.N + cell] = (double)hy.uy;
+        u[2 * p.N + cell] = (double)hy.uz;
+    }
+}
+
+// ---- initial state: equilibrium at the cell, then the inverse of the pull -----------------
+template <int D, class S>
+__global__ void __launch_bounds__(kBlock) k_equilibrium(S* __restrict__ dst, const typename Codec<S>::R* __restrict__ Ff,
+                                                       Params p, const double* __restrict__ rho, const double* __restrict__ u) {
+    using R = typename Codec<S>::R;
+    constexpr int Q = Lat<D>::Q;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= p.nx || y >= p.ny) return;
+    const unsigned cell = (unsigned)((z * p.ny + y) * p.nx + x);
+    R F[3];
+    load_force<R>(Ff, p, cell, F);
+    const double r = rho ? rho[cell] : 1.0;
+    double ux = u ? u[cell] : 0.0, uy = u ? u[p.N + cell] : 0.0, uz = (u && D == 3) ? u[2 * p.N + cell] : 0.0;
+    if (p.reduced) {   // momentum rho0 u: centre the equilibrium on rho0 u / rho
+        ux *= p.rho0 / r;
+        uy *= p.rho0 / r;
+        uz *= p.rho0 / r;
+    }
+    R m[Q];
+    equilibrium<D, R>(m, (R)r, (R)ux, (R)uy, (R)uz, F);
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        Codec<S>::st(dst + (long long)i * p.N + cell, m[slot<D>(i)] * (R)inv_weight<D>(i));
+}
+
+// s_i(x) = fbar_i(x + e_i), or the reflected value when x + e_i is behind a wall
+template <int D, class S>
+__global__ void __launch_bounds__(kBlock) k_unstream(const S* __restrict__ fb, S* __restrict__ dst, Params p) {
+    using R = typename Codec<S>::R;
+    constexpr int Q = Lat<D>::Q;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= p.nx || y >= p.ny) return;
+    const unsigned cell = (unsigned)((z * p.ny + y) * p.nx + x);
+    const int xyz[3] = {x, y, z};
+    const int n[3] = {p.nx, p.ny, p.nz};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int e[3] = {Lat<D>::ex(i), Lat<D>::ey(i), Lat<D>::ez(i)};
+        int t[3];
+        bool out = false;
+        R wsum[3] = {0, 0, 0}, cnt = 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            t[a] = xyz[a] + e[a];
+            if (t[a] < 0 || t[a] >= n[a]) {
+                if (p.bc[a] == 0) {
+                    t[a] += (t[a] < 0) ? n[a] : -n[a];
+                } else {
+                    const int side = (t[a] < 0) ? 0 : 1;
+                    out = true;
+                    cnt += 1;
+                    wsum[0] += (R)p.uw[a][side][0];
+                    wsum[1] += (R)p.uw[a][side][1];
+                    wsum[2] += (R)p.uw[a][side][2];
+                    t[a] = xyz[a];
+                }
+            }
+        }
+        R d;
+        if (out) {
+            const R eu = (R)e[0] * wsum[0] + (R)e[1] * wsum[1] + (R)e[2] * wsum[2];
+            d = Codec<S>::ld(fb + (long long)Lat<D>::opp(i) * p.N + cell) + R(6) * eu / cnt;
+        } else {
+            const unsigned tc = (unsigned)((t[2] * p.ny + t[1]) * p.nx + t[0]);
+            d = Codec<S>::ld(fb + (long long)i * p.N + tc);
+        }
+        Codec<S>::st(dst + (long long)i * p.N + cell, d);
+    }
+}
+
+// ---- deterministic FP64 reductions -------------------------------------------------------
+constexpr int kRedThreads = 256;
+constexpr int kRedMaxBlocks = 1216;     // 8 blocks on each of 152 SMs
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// per-block partial sums of {rho, rho ux, rho uy, rho uz, rho |u|^2 / 2} into part[block*5 + k]
+template <int D, class S, bool WALLS>
+__global__ void __launch_bounds__(kRedThreads) k_reduce_partial(const S* __restrict__ src,
+                                                               const typename Codec<S>::R* __restrict__ Ff,
+                                                               Params p, double* __restrict__ part) {
+    using R = typename Codec<S>::R;
+    double acc[5] = {0, 0, 0, 0, 0};
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < p.N; c += stride) {
+        const int x = (int)(c % p.nx);
+        const long long r = c / p.nx;
+        const int y = (int)(r % p.ny);
+        const int z = (int)(r / p.ny);
+        R h[Lat<D>::Q];
+        gather<D, S, WALLS>(src, x, y, z, p, h);
+        R F[3];
+        load_force<R>(Ff, p, (unsigned)c, F);
+        const Hydro<D, R> hy = hydro<D, R>(h, F, p);
+        const double rho = 1.0 + (double)hy.drho;
+        const double jx = (double)hy.jx, jy = (double)hy.jy, jz = (double)hy.jz;
+        const double ux = (double)hy.ux, uy = (double)hy.uy, uz = (double)hy.uz;
+        acc[0] += rho;
+        acc[1] += rho * ux;
+        acc[2] += rho * uy;
+        acc[3] += rho * uz;
+        acc[4] += 0.5 * rho * (ux * ux + uy * uy + uz * uz);
+        (void)jx; (void)jy; (void)jz;
+    }
+    __shared__ double sh[kRedThreads / 32][5];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const double v = warp_sum(acc[k]);
+        if (lane == 0) sh[wid][k] = v;
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            double v = (lane < kRedThreads / 32) ? sh[lane][k] : 0.0;
+            v = warp_sum(v);
+            if (lane == 0) part[blockIdx.x * 5 + k] = v;
+        }
+    }
+}
+
+// sum nblocks partials in a fixed order into out[5]
+static __global__ void __launch_bounds__(kRedThreads) k_reduce_final(const double* __restrict__ part, int nblocks,
+                                                             double* __restrict__ out) {
+    __shared__ double sh[kRedThreads / 32][5];
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) acc[k] += part[b * 5 + k];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const double v = warp_sum(acc[k]);
+        if (lane == 0) sh[wid][k] = v;
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            double v = (lane < kRedThreads / 32) ? sh[lane][k] : 0.0;
+            v = warp_sum(v);
+            if (lane == 0) out[k] = v;
+        }
+    }
+}
+
+// FP64 [3][N] force field -> arithmetic type
+template <class R>
+__global__ void k_convert_force(const double* __restrict__ in, R* __restrict__ out, long long n) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) out[k] = (R)in[k];
+}
+
+// ------------------------------------------------------------------------------------------
+// Host launchers (instantiated in inst_*.cu)
+// ------------------------------------------------------------------------------------------
+inline bool has_walls(const Params& p) { return p.bc[0] || p.bc[1] || p.bc[2]; }
+
+template <int D, class S>
+cudaError_t launch_step(const void* src, void* dst, const void* Ff, const Params& p, cudaStream_t st) {
+    using R = typename Codec<S>::R;
+    const dim3 b = cell_block(p.nx), g = cell_grid(p, b);
+    if (has_walls(p))
+        k_step<D, S, true><<<g, b, 0, st>>>((const S*)src, (S*)dst, (const R*)Ff, p);
+    else
+        k_step<D, S, false><<<g, b, 0, st>>>((const S*)src, (S*)dst, (const R*)Ff, p);
+    return cudaGetLastError();
+}
+
+template <int D, class S>
+cudaError_t launch_moments(const void* src, const void* Ff, const Params& p, double* rho, double* u, cudaStream_t st) {
+    using R = typename Codec<S>::R;
+    const dim3 b = cell_block(p.nx), g = cell_grid(p, b);
+    if (has_walls(p))
+        k_moments<D, S, true><<<g, b, 0, st>>>((const S*)src, (const R*)Ff, p, rho, u);
+    else
+        k_moments<D, S, false><<<g, b, 0, st>>>((const S*)src, (const R*)Ff, p, rho, u);
+    return cudaGetLastError();
+}
+
+template <int D, class S>
+cudaError_t launch_init(void* tmp, void* dst, const void* Ff, const Params& p, const double* rho, const double* u,
+                        cudaStream_t st) {
+    using R = typename Codec<S>::R;
+    const dim3 b = cell_block(p.nx), g = cell_grid(p, b);
+    k_equilibrium<D, S><<<g, b, 0, st>>>((S*)tmp, (const R*)Ff, p, rho, u);
+    k_unstream<D, S><<<g, b, 0, st>>>((const S*)tmp, (S*)dst, p);
+    return cudaGetLastError();
+}
+
+inline int reduce_blocks(const Params& p) {
+    long long nb = (p.N + kRedThreads - 1) / kRedThreads;
+    return (int)(nb < kRedMaxBlocks ? nb : kRedMaxBlocks);
+}
+
+template <int D, class S>
+cudaError_t launch_reduce(const void* src, const void* Ff, const Params& p, double* part, double* out, cudaStream_t st) {
+    using R = typename Codec<S>::R;
+    const int nb = reduce_blocks(p);
+    if (has_walls(p))
+        k_reduce_partial<D, S, true><<<nb, kRedThreads, 0, st>>>((const S*)src, (const R*)Ff, p, part);
+    else
+        k_reduce_partial<D, S, false><<<nb, kRedThreads, 0, st>>>((const S*)src, (const R*)Ff, p, part);
+    k_reduce_final<<<1, kRedThreads, 0, st>>>(part, nb, out);
+    return cudaGetLastError();
+}
+
+}  // namespace cm
+
+// Explicit-instantiation helpers
+#define CM_INSTANTIATE(D, S)                                                                               \
+    template cudaError_t cm::launch_step<D, S>(const void*, void*, const void*, const cm::Params&, cudaStream_t); \
+    template cudaError_t cm::launch_moments<D, S>(const void*, const void*, const cm::Params&, double*, double*, \
+                                                  cudaStream_t);                                           \
+    template cudaError_t cm::launch_init<D, S>(void*, void*, const void*, const cm::Params&, const double*,  \
+                                               const double*, cudaStream_t);                               \
+    template cudaError_t cm::launch_reduce<D, S>(const void*, const void*, const cm::Params&, double*, double*, \
+                                                 cudaStream_t);

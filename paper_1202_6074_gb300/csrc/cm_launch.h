@@ -1,0 +1,30 @@
+// Declarations of the host launchers defined in cm_kernels.cuh and instantiated in inst_*.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "cm_core.cuh"
+
+namespace cm {
+template <int D, class S>
+cudaError_t launch_step(const void* src, void* dst, const void* Ff, const Params& p, cudaStream_t st);
+template <int D, class S>
+cudaError_t launch_moments(const void* src, const void* Ff, const Params& p, double* rho, double* u, cudaStream_t st);
+template <int D, class S>
+cudaError_t launch_init(void* tmp, void* dst, const void* Ff, const Params& p, const double* rho, const double* u,
+                        cudaStream_t st);
+template <int D, class S>
+cudaError_t launch_reduce(const void* src, const void* Ff, const Params& p, double* part, double* out, cudaStream_t st);
+cudaError_t launch_convert_force(const double* in, void* out, long long n, bool fp64, cudaStream_t st);
+
+template <int D, class R>
+cudaError_t launch_adjoint_terminal(const void* state, const void* Ff, const Params& p, const double* dLdu,
+                                    const double* dLdrho, void* lambda, double* dLdF, cudaStream_t st);
+template <int D, class R>
+cudaError_t launch_adjoint_step(const void* state, const void* Ff, const Params& p, const void* lam_in, void* lam_out,
+                                double* dLdF, cudaStream_t st);
+
+constexpr int kReduceMaxBlocks = 1216;
+}  // namespace cm

@@ -33,24 +33,25 @@ def rest(nx, ny, nz=1, background=(0.0, 0.0, 0.0)):
     return rho, u
 
 
-def taylor_green(nx, ny, nz, u0=0.05, background=(0.0, 0.0, 0.0), two_d=False):
+def taylor_green(nx, ny, nz, u0=0.05, background=(0.0, 0.0, 0.0), two_d=False, xp=np, device=None):
     """u = u0 sin x cos y cos z, v = -u0 cos x sin y cos z, w = 0 (x = 2 pi i / L), plus U.
 
     Pressure of the incompressible solution, p = rho0 u0^2 / 16 (cos 2x + cos 2y)(cos 2z + 2),
     sets rho = 1 + 3 p. two_d drops the z dependence (exact Navier-Stokes solution decaying
-    as exp(-2 nu k^2 t) for a square box).
+    as exp(-2 nu k^2 t) for a square box). xp = numpy or torch (with ``device``).
     """
-    x, y, z = _grid(nx, ny, nz)
-    kx, ky, kz = 2 * math.pi / nx, 2 * math.pi / ny, 2 * math.pi / nz
-    X, Y, Z = kx * x, ky * y, kz * z
-    cz = np.ones_like(Z) if two_d else np.cos(Z)
-    u = np.zeros((3, nz, ny, nx))
-    u[0] = u0 * np.sin(X) * np.cos(Y) * cz
-    u[1] = -u0 * np.cos(X) * np.sin(Y) * cz
+    kw = {} if xp is np else {"device": device, "dtype": xp.float64}
+    X = (xp.arange(nx, **kw) * (2 * math.pi / nx)).reshape(1, 1, nx)
+    Y = (xp.arange(ny, **kw) * (2 * math.pi / ny)).reshape(1, ny, 1)
+    Z = (xp.arange(nz, **kw) * (2 * math.pi / nz)).reshape(nz, 1, 1)
+    cz = xp.ones_like(Z) if two_d else xp.cos(Z)
+    u = xp.zeros((3, nz, ny, nx), **kw)
+    u[0] = u0 * xp.sin(X) * xp.cos(Y) * cz
+    u[1] = -u0 * xp.cos(X) * xp.sin(Y) * cz
     if two_d:
-        p = u0 * u0 / 4.0 * (np.cos(2 * X) + np.cos(2 * Y))
+        p = u0 * u0 / 4.0 * (xp.cos(2 * X) + xp.cos(2 * Y)) + 0.0 * Z
     else:
-        p = u0 * u0 / 16.0 * (np.cos(2 * X) + np.cos(2 * Y)) * (np.cos(2 * Z) + 2.0)
+        p = u0 * u0 / 16.0 * (xp.cos(2 * X) + xp.cos(2 * Y)) * (xp.cos(2 * Z) + 2.0)
     rho = 1.0 + 3.0 * p
     for d in range(3):
         u[d] += background[d]
@@ -69,22 +70,38 @@ def _shell_vectors(kmax2):
     return reps
 
 
-def hit_forcing(nx, ny, nz, seed=1, f_rms=5e-6):
-    """F = sum over the 16 +-pairs with 0 < |k| <= 2 of A_k cos(k.x + phi_k), A_k perp k."""
+def hit_modes(seed=1, f_rms=5e-6):
+    """The 16 +-pairs with 0 < |k| <= 2: (k, A_k perp k, phi_k), scaled so that rms |F| = f_rms.
+
+    On a periodic box the modes are orthogonal and <cos^2> = 1/2, so rms^2 = sum |A_k|^2 / 2.
+    """
     rng = np.random.default_rng(seed)
-    x, y, z = _grid(nx, ny, nz)
-    F = np.zeros((3, nz, ny, nx))
+    modes = []
     for k in _shell_vectors(4):
         kv = np.array(k, dtype=np.float64)
         a = rng.standard_normal(3)
         a -= kv * (a @ kv) / (kv @ kv)
         phi = rng.uniform(0.0, 2 * math.pi)
-        arg = 2 * math.pi * (k[0] * x / nx + k[1] * y / ny + k[2] * z / nz) + phi
-        c = np.cos(arg)
+        modes.append((k, a, phi))
+    rms = math.sqrt(sum(float(a @ a) for _, a, _ in modes) / 2.0)
+    return [(k, a * (f_rms / rms), phi) for k, a, phi in modes]
+
+
+def hit_forcing(nx, ny, nz, seed=1, f_rms=5e-6, xp=np, device=None):
+    """F = sum_k A_k cos(2 pi k.x / L + phi_k) as a [3, nz, ny, nx] float64 array.
+
+    xp is numpy (default) or torch (then ``device`` places the field, e.g. on the GPU).
+    """
+    kw = {} if xp is np else {"device": device, "dtype": xp.float64}
+    ax = [xp.arange(n, **kw) * (1.0 / n) if xp is np else xp.arange(n, **kw) / n for n in (nx, ny, nz)]
+    F = xp.zeros((3, nz, ny, nx), **kw)
+    for k, a, phi in hit_modes(seed, f_rms):
+        arg = (2 * math.pi * k[2] * ax[2]).reshape(nz, 1, 1) + (2 * math.pi * k[1] * ax[1]).reshape(1, ny, 1) \
+            + (2 * math.pi * k[0] * ax[0]).reshape(1, 1, nx) + phi
+        c = xp.cos(arg)
         for d in range(3):
-            F[d] += a[d] * c
-    rms = math.sqrt(float(np.mean(np.sum(F * F, axis=0))))
-    return F * (f_rms / rms)
+            F[d] += float(a[d]) * c
+    return F
 
 
 def random_solenoidal(nx, ny, nz, seed=2, kmax=4, u_rms=0.02):

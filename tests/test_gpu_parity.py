@@ -1,0 +1,303 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 CPU oracle.
+
+Tolerances (derived from the arithmetic):
+  * FP64 storage (FP64 arithmetic): element-wise |d_gpu - d_oracle| <= 1e-13 after one step,
+    trajectories rel-L2 <= 1e-11.
+  * FP32: one step element-wise |d_gpu - d_oracle| <= 4e-6 (about 1000 FP32 operations on
+    O(0.1) quantities); trajectories rel-L2(u) <= 1e-5 (the stated target).
+  * BF16 / FP16 storage: one step |d_gpu - d_oracle| <= |d| 2^-8 (2^-11) + 4e-6, i.e. one
+    rounding of the stored deviation; trajectories rel-L2(u) <= 2e-3 (the stated target).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import helpers as H
+from oracle.solver import OracleSim
+from oracle.collision import Params
+from paper_1202_6074_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+ONE_STEP_ATOL = {"f64": 1e-13, "f32": 4e-6, "bf16": 4e-6, "f16": 4e-6}
+ONE_STEP_RTOL = {"f64": 0.0, "f32": 0.0, "bf16": 2.0 ** -8, "f16": 2.0 ** -11}
+
+
+@pytest.fixture(scope="module")
+def cm():
+    import __graft_entry__ as G
+
+    G.build()
+    from paper_1202_6074_gb300 import cmlbm
+
+    assert torch.cuda.is_available()
+    return cmlbm
+
+
+def _params(kw):
+    return Params(tau=kw.get("tau", 0.8), omega_bulk=kw.get("omega_bulk", 0.0), omega3=kw.get("omega_3", 1.0),
+                  omega4=kw.get("omega_4", 1.0), cs_smag=kw.get("smagorinsky_cs", 0.0),
+                  attractor=kw.get("attractor", "maxwell"),
+                  reduced_compressibility=kw.get("reduced_compressibility", False), rho0=kw.get("rho0", 1.0))
+
+
+def _pair(cm, lattice, shape, storage, rho, u, F=None, uniform=(0.0, 0.0, 0.0), **kw):
+    nz, ny, nx = shape
+    bc = kw.get("bc", ("periodic",) * 3)
+    uw = kw.get("wall_velocity", H.zero_walls())
+    s = cm.Solver(lattice=lattice, nx=nx, ny=ny, nz=nz, storage=storage, **kw)
+    s.set_force(uniform, None if F is None else torch.tensor(F, device="cuda"))
+    s.init(None if rho is None else torch.tensor(rho, device="cuda"), None if u is None else torch.tensor(u, device="cuda"))
+    o = OracleSim(lattice, nx, ny, nz, _params(kw), bc=bc, wall_velocity=uw, van_driest=kw.get("van_driest"))
+    o.set_force(uniform, None if F is None else torch.tensor(F))
+    o.init(None if rho is None else torch.tensor(rho), None if u is None else torch.tensor(u))
+    return s, o
+
+
+CASES = {
+    "periodic_tgv": dict(lattice="D3Q27", shape=(7, 10, 150), flow="tgv", kw=dict(tau=0.62, omega_3=1.2, omega_4=0.9)),
+    "walls_les_field": dict(lattice="D3Q27", shape=(6, 9, 37), flow="channel",
+                            kw=dict(tau=0.52, smagorinsky_cs=0.15, van_driest=(26.0, 8.0),
+                                    bc=("periodic", "bounceback", "periodic"),
+                                    wall_velocity=[[[0, 0, 0], [0, 0, 0]], [[0.02, 0, 0.01], [-0.03, 0.0, 0.0]],
+                                                   [[0, 0, 0], [0, 0, 0]]])),
+    "all_walls_bulk": dict(lattice="D3Q27", shape=(5, 6, 7), flow="tgv",
+                           kw=dict(tau=0.7, omega_bulk=1.3, bc=("bounceback",) * 3,
+                                   wall_velocity=[[[0, 0.01, 0], [0, 0, 0.02]], [[0.03, 0, 0], [0, 0, -0.01]],
+                                                  [[0.01, 0.01, 0], [-0.02, 0, 0]]])),
+    "d2q9_channel": dict(lattice="D2Q9", shape=(1, 12, 140), flow="channel",
+                         kw=dict(tau=0.8, omega_3=8.0 / 9.0, bc=("periodic", "bounceback", "periodic"),
+                                 wall_velocity=[[[0, 0, 0], [0, 0, 0]], [[0.05, 0, 0], [0.05, 0, 0]], [[0, 0, 0], [0, 0, 0]]])),
+    "d2q9_les_tgv": dict(lattice="D2Q9", shape=(1, 33, 31), flow="tgv", kw=dict(tau=0.55, smagorinsky_cs=0.2)),
+}
+
+
+def _inputs(case):
+    nz, ny, nx = case["shape"]
+    two_d = case["lattice"] == "D2Q9"
+    if case["flow"] == "tgv":
+        rho, u = W.taylor_green(nx, ny, nz, u0=0.05, background=(0.02, -0.01, 0.0 if two_d else 0.015), two_d=two_d)
+        F = W.gaussian_force(nx, ny, nz, seed=3, std=1e-4)
+    else:
+        rho, u, F = W.channel(nx, ny, nz, u_tau=0.01, seed=5)
+        F = F + W.gaussian_force(nx, ny, nz, seed=4, std=1e-5)
+    if two_d:
+        u[2] = 0.0
+        F[2] = 0.0
+    return rho, u, F
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "bf16", "f16"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_one_step_elementwise(cm, name, storage):
+    case = CASES[name]
+    rho, u, F = _inputs(case)
+    s, o = _pair(cm, case["lattice"], case["shape"], storage, rho, u, F, **case["kw"])
+    # both sides start from the same (GPU-encoded) state
+    s0 = s.get_state()
+    o.set_state(H.decode(s0, case["lattice"]))
+    s.step(1)
+    o.step(1)
+    got = H.decode(s.get_state(), case["lattice"])
+    ref = o.s
+    lat = H.lattice(case["lattice"])
+    w = lat.w.view(-1, 1, 1, 1)
+    d_got, d_ref = got / w - 1, ref / w - 1
+    tol = ONE_STEP_ATOL[storage] + ONE_STEP_RTOL[storage] * d_ref.abs()
+    err = (d_got - d_ref).abs()
+    assert bool((err <= tol).all()), f"max |dd| = {err.max().item():.3e}"
+    s.close()
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "bf16", "f16"])
+@pytest.mark.parametrize("name", ["periodic_tgv", "walls_les_field", "all_walls_bulk", "d2q9_channel"])
+def test_init_returns_requested_fields(cm, name, storage):
+    case = CASES[name]
+    rho, u, F = _inputs(case)
+    s, _ = _pair(cm, case["lattice"], case["shape"], storage, rho, u, F, **case["kw"])
+    r, uu = s.moments()
+    tol = {"f64": 1e-14, "f32": 1e-6, "bf16": 3e-3, "f16": 5e-4}[storage]
+    assert (r.cpu() - torch.tensor(rho)).abs().max().item() < tol
+    assert (uu.cpu() - torch.tensor(u)).abs().max().item() < tol * 0.2 + 1e-15
+    s.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_trajectory_fp64(cm, name):
+    case = CASES[name]
+    rho, u, F = _inputs(case)
+    s, o = _pair(cm, case["lattice"], case["shape"], "f64", rho, u, F, **case["kw"])
+    s.step(20)
+    o.step(20)
+    rg, ug = s.moments()
+    ro, uo = o.moments()
+    assert H.rel_l2(ug, uo) < 1e-11
+    assert (rg.cpu() - ro).abs().max().item() < 1e-13
+    s.close()
+
+
+@pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("bf16", 2e-3), ("f16", 2e-3)])
+def test_trajectory_reduced_precision_tgv(cm, storage, tol):
+    """D3Q27 Taylor-Green 24^3 with background velocity and force field, 60 steps."""
+    n = 24
+    rho, u = W.taylor_green(n, n, n, u0=0.05, background=(0.05, 0.03, 0.0))
+    F = W.gaussian_force(n, n, n, seed=3, std=1e-5)
+    s, o = _pair(cm, "D3Q27", (n, n, n), storage, rho, u, F, tau=0.55)
+    s.step(60)
+    o.step(60)
+    _, ug = s.moments()
+    _, uo = o.moments()
+    # velocity error measured on the fluctuation about the background flow
+    bg = torch.tensor([0.05, 0.03, 0.0], dtype=torch.float64).view(3, 1, 1, 1)
+    err = H.rel_l2(ug.cpu() - bg, uo - bg)
+    assert err < tol, f"{storage}: rel-L2(u - U) = {err:.3e}"
+    s.close()
+
+
+def test_poiseuille_cfg1_fp64_matches_oracle_and_closed_form(cm):
+    """64 x 32 D2Q9 FP64 body-force channel, tau = 0.8, F = 1e-6, 5000 steps; and the rerun with
+    walls and fluid moving at U = 0.05 (Galilean invariance)."""
+    nx, ny, F, tau, steps = 64, 32, 1e-6, 0.8, 5000
+    nu = (tau - 0.5) / 3
+    bc = ("periodic", "bounceback", "periodic")
+    res = {}
+    for U in (0.0, 0.05):
+        uw = [[[0, 0, 0], [0, 0, 0]], [[U, 0, 0], [U, 0, 0]], [[0, 0, 0], [0, 0, 0]]]
+        rho, u = W.rest(nx, ny, 1, background=(U, 0, 0))
+        s, o = _pair(cm, "D2Q9", (1, ny, nx), "f64", rho, u, None, uniform=(F, 0, 0), tau=tau, bc=bc, wall_velocity=uw)
+        s.step(steps)
+        o.step(steps)
+        _, ug = s.moments()
+        _, uo = o.moments()
+        assert H.rel_l2(ug.cpu() - U, uo - U) < 1e-10
+        res[U] = ug.cpu()[0, 0, :, 0].numpy() - U
+        s.close()
+    # start-up closed form (series), eta = y + 1/2, H = ny
+    eta = np.arange(ny) + 0.5
+    H_ = float(ny)
+    ref = F / (2 * nu) * eta * (H_ - eta)
+    for n in range(1, 200, 2):
+        ref -= 4 * F * H_ ** 2 / (nu * math.pi ** 3 * n ** 3) * np.sin(n * math.pi * eta / H_) * math.exp(
+            -n * n * math.pi ** 2 * nu * steps / H_ ** 2)
+    assert np.abs(res[0.0] - ref).max() / ref.max() < 1e-2
+    assert np.abs(res[0.05] - res[0.0]).max() / ref.max() < 1e-3
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_reduce_matches_compensated_sum(cm, storage):
+    n = (19, 23, 130)
+    rho, u = W.taylor_green(n[2], n[1], n[0], u0=0.05, background=(0.01, 0.02, 0.03))
+    s, _ = _pair(cm, "D3Q27", n, storage, rho, u, None, uniform=(1e-5, 0, 0), tau=0.6)
+    s.step(3)
+    red = s.reduce()
+    r, uu = s.moments()
+    r = r.cpu().numpy().ravel()
+    uu = uu.cpu().numpy().reshape(3, -1)
+    ref = [math.fsum(r), math.fsum(r * uu[0]), math.fsum(r * uu[1]), math.fsum(r * uu[2]),
+           math.fsum(0.5 * r * (uu ** 2).sum(0))]
+    for k in range(5):
+        assert abs(red[k] - ref[k]) <= 1e-12 * abs(ref[k]) + 1e-300, (k, red[k], ref[k])
+    s.close()
+
+
+def test_mass_drift_fp64(cm):
+    """Mass is conserved to round-off in FP64 with walls, moving walls, LES and a force field."""
+    case = CASES["walls_les_field"]
+    rho, u, F = _inputs(case)
+    s, _ = _pair(cm, "D3Q27", case["shape"], "f64", rho, u, F, **case["kw"])
+    m0 = s.reduce()[0]
+    s.step(200)
+    m1 = s.reduce()[0]
+    assert abs(m1 - m0) / m0 < 1e-12
+    s.close()
+
+
+def test_momentum_gain_equals_force_fp64(cm):
+    n = 12
+    rho, u = W.random_solenoidal(n, n, n, seed=7, u_rms=0.02)
+    F = W.gaussian_force(n, n, n, seed=8, std=1e-4)
+    s, _ = _pair(cm, "D3Q27", (n, n, n), "f64", rho, u, F, tau=0.55, smagorinsky_cs=0.1)
+    a = s.reduce()
+    s.step(10)
+    b = s.reduce()
+    for d in range(3):
+        assert abs((b[1 + d] - a[1 + d]) - 10 * F[d].sum()) < 1e-12
+    s.close()
+
+
+def test_deterministic(cm):
+    case = CASES["walls_les_field"]
+    rho, u, F = _inputs(case)
+    outs = []
+    for _ in range(2):
+        s, _ = _pair(cm, "D3Q27", case["shape"], "f32", rho, u, F, **case["kw"])
+        s.step(7)
+        outs.append((s.get_state().cpu(), s.reduce()))
+        s.close()
+    assert torch.equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1]
+
+
+def test_host_buffers_match_device(cm):
+    n = (4, 6, 40)
+    rho, u = W.taylor_green(n[2], n[1], n[0], u0=0.03)
+    F = W.gaussian_force(n[2], n[1], n[0], seed=9, std=1e-5)
+    a = cm.Solver(lattice="D3Q27", nx=n[2], ny=n[1], nz=n[0], storage="f32", tau=0.6)
+    a.set_force((0, 0, 0), F)              # numpy -> host path
+    a.init(rho, u)
+    a.step(5)
+    ra, ua = a.moments(host=True)
+    b = cm.Solver(lattice="D3Q27", nx=n[2], ny=n[1], nz=n[0], storage="f32", tau=0.6)
+    b.set_force((0, 0, 0), torch.tensor(F, device="cuda"))
+    b.init(torch.tensor(rho, device="cuda"), torch.tensor(u, device="cuda"))
+    b.step(5)
+    rb, ub = b.moments()
+    assert np.array_equal(ra, rb.cpu().numpy()) and np.array_equal(ua, ub.cpu().numpy())
+    a.close()
+    b.close()
+
+
+def test_step_buffers_equals_step(cm):
+    n = (5, 8, 33)
+    rho, u = W.taylor_green(n[2], n[1], n[0], u0=0.03)
+    s = cm.Solver(lattice="D3Q27", nx=n[2], ny=n[1], nz=n[0], storage="f32", tau=0.6)
+    s.init(torch.tensor(rho, device="cuda"), torch.tensor(u, device="cuda"))
+    a = s.get_state()
+    b = s.new_state()
+    s.step_buffers(a, b)
+    s.step(1)
+    assert torch.equal(s.get_state(), b)
+    r1, u1 = s.moments()
+    r2, u2 = s.moments(state=b)
+    assert torch.equal(r1, r2) and torch.equal(u1, u2)
+    s.close()
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 1, 5), (3, 1, 1), (2, 2, 2)])
+def test_degenerate_grids(cm, shape):
+    """One-cell axes wrap onto themselves (periodic) or reflect (walls)."""
+    nz, ny, nx = shape
+    rho, u = W.taylor_green(nx, ny, nz, u0=0.02, background=(0.01, 0.0, 0.0))
+    for bc in (("periodic",) * 3, ("bounceback",) * 3):
+        s, o = _pair(cm, "D3Q27", shape, "f64", rho, u, None, uniform=(1e-4, 0, 0), tau=0.7, bc=bc)
+        s.step(3)
+        o.step(3)
+        got = H.decode(s.get_state(), "D3Q27")
+        assert (got - o.s).abs().max().item() < 1e-14
+        s.close()
+
+
+def test_invalid_arguments_return_errors(cm):
+    s = cm.Solver(lattice="D3Q27", nx=4, ny=4, nz=4, storage="f32")
+    with pytest.raises(cm.CmlbmError) as e:
+        s.step(-1)
+    assert e.value.code == cm.ERR_INVALID
+    bad = s.new_state()
+    with pytest.raises(cm.CmlbmError):
+        s.step_buffers(bad, bad)
+    with pytest.raises(cm.CmlbmError) as e:
+        s.adjoint_terminal(bad, torch.zeros(3, 64, dtype=torch.float64, device="cuda"), bad,
+                           torch.zeros(3, 64, dtype=torch.float64, device="cuda"))
+    s.close()
