@@ -70,7 +70,7 @@ typedef struct cmlbm cmlbm_t;
 
 /*
  * Configuration. Fill with cmlbm_config_default() and override.
- *   lattice, nx, ny, nz   D2Q9 needs nz == 1. Each size >= 1, N * Q < 2^40.
+ *   lattice, nx, ny, nz   D2Q9 needs nz == 1. Each size >= 1, N < 2^31 and Q * N < 2^32.
  *   storage               arithmetic is FP64 for CMLBM_F64 storage and FP32 otherwise.
  *   bc[3]                 per axis (x, y, z). Bounce-back puts half-way walls outside the
  *                         first and last cells of that axis (paper silent on boundaries):

@@ -28,9 +28,9 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def _compile(nvcc, src, verbose):
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-    cmd = [nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj]
+def _compile(nvcc, src, verbose, extra=(), build_dir=BUILD):
+    obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
+    cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -39,31 +39,37 @@ def _compile(nvcc, src, verbose):
     return obj, r.stderr
 
 
-def build(force=False, verbose=False, jobs=None):
-    """Compile every .cu and link libcmlbm.so; skipped when the library is newer than all sources."""
+def build(force=False, verbose=False, jobs=None, extra_flags=(), out=None):
+    """Compile every .cu and link libcmlbm.so; skipped when the library is newer than all sources.
+
+    extra_flags are passed to every nvcc compile (e.g. -DCM_STEP_MIN_BLOCKS=5); out is another
+    library path (with its own object directory) for such variants.
+    """
+    lib = out or LIB
+    build_dir = BUILD if out is None else out + ".objs"
     srcs = sources()
     deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     deps.append(os.path.join(HERE, "..", "include", "cmlbm.h"))
-    if not force and os.path.exists(LIB):
-        t = os.path.getmtime(LIB)
+    if not force and os.path.exists(lib):
+        t = os.path.getmtime(lib)
         if all(os.path.getmtime(d) <= t for d in deps):
-            return LIB
+            return lib
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    os.makedirs(build_dir, exist_ok=True)
     jobs = jobs or min(len(srcs), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(jobs) as ex:
-        results = list(ex.map(lambda s: _compile(nvcc, s, verbose), srcs))
+        results = list(ex.map(lambda s: _compile(nvcc, s, verbose, tuple(extra_flags), build_dir), srcs))
     objs = [o for o, _ in results]
     if verbose:
         for _, log in results:
             sys.stderr.write(log)
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

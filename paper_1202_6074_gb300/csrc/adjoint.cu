@@ -1,23 +1,340 @@
-// Adjoint kernels (reverse mode of one stream-and-collide step).
+// Adjoint (reverse mode) of one stream-and-collide step and of the terminal velocity read-out.
+//
+// Forward step per cell x: g = pull(s_t)(x), s_{t+1}(x) = C(g, F(x)) with C the collision of
+// cm_core.cuh. With lambda = dL/ds (post-collision populations, not the encoded deviations):
+//   nu(x)       = J_C(g(x))^T lambda_{t+1}(x)             (per-cell vector-Jacobian product)
+//   lambda_t    = pull^T nu                               (a permutation: scatter without atomics)
+//   dL/dF(x)   += (dC/dF)^T lambda_{t+1}(x)
+// The collision is written here in plain central moments of fbar (same function as the
+// forward kernel's deviation form):
+//   kbar = T(u) g,  post = M(kbar, rho, F),  s = T(u)^-1 post,  u = (sum g e + F/2) / rho.
+// Derivatives of the transforms with respect to u use d(T g)_a / du_x = -alpha kbar_(a - e_x)
+// (alpha the x exponent of monomial a), so no intermediate sweep state is needed:
+//   from the forward transform:  ubar_x -= sum_a kbarbar_a alpha kbar_(a-e_x)
+//   from the inverse transform:  ubar_x += sum_a postbar_a alpha post_(a-e_x).
 #include "cm_kernels.cuh"
 #include "cm_launch.h"
 
 namespace cm {
-template <int D, class R>
-cudaError_t launch_adjoint_terminal(const void*, const void*, const Params&, const double*, const double*, void*,
-                                    double*, cudaStream_t) {
-    return cudaErrorNotSupported;
+namespace {
+
+// transpose of the 1D forward transform (f-, f0, f+) -> (m0, m1, m2)
+template <class R> __device__ __forceinline__ void fwd1_T(R& a, R& b, R& c, R u) {
+    const R m0 = a, m1 = b, m2 = c;
+    const R em = R(-1) - u, e0 = -u, ep = R(1) - u;
+    a = m0 + em * m1 + em * em * m2;
+    b = m0 + e0 * m1 + e0 * e0 * m2;
+    c = m0 + ep * m1 + ep * ep * m2;
 }
-template <int D, class R>
-cudaError_t launch_adjoint_step(const void*, const void*, const Params&, const void*, void*, double*, cudaStream_t) {
-    return cudaErrorNotSupported;
+// transpose of the 1D inverse transform (m0, m1, m2) -> (f-, f0, f+)
+template <class R> __device__ __forceinline__ void inv1_T(R& a, R& b, R& c, R u) {
+    const R fm = a, f0 = b, fp = c;
+    const R uu = u * u;
+    a = R(0.5) * (uu - u) * fm + (R(1) - uu) * f0 + R(0.5) * (uu + u) * fp;
+    b = R(0.5) * (R(2) * u - R(1)) * fm - R(2) * u * f0 + R(0.5) * (R(2) * u + R(1)) * fp;
+    c = R(0.5) * fm - f0 + R(0.5) * fp;
 }
-template cudaError_t launch_adjoint_terminal<3, double>(const void*, const void*, const Params&, const double*, const double*, void*, double*, cudaStream_t);
-template cudaError_t launch_adjoint_terminal<3, float>(const void*, const void*, const Params&, const double*, const double*, void*, double*, cudaStream_t);
-template cudaError_t launch_adjoint_terminal<2, double>(const void*, const void*, const Params&, const double*, const double*, void*, double*, cudaStream_t);
-template cudaError_t launch_adjoint_terminal<2, float>(const void*, const void*, const Params&, const double*, const double*, void*, double*, cudaStream_t);
-template cudaError_t launch_adjoint_step<3, double>(const void*, const void*, const Params&, const void*, void*, double*, cudaStream_t);
-template cudaError_t launch_adjoint_step<3, float>(const void*, const void*, const Params&, const void*, void*, double*, cudaStream_t);
-template cudaError_t launch_adjoint_step<2, double>(const void*, const void*, const Params&, const void*, void*, double*, cudaStream_t);
-template cudaError_t launch_adjoint_step<2, float>(const void*, const void*, const Params&, const void*, void*, double*, cudaStream_t);
+
+template <int D, class R> __device__ __forceinline__ void fwd_T(R (&m)[Lat<D>::Q], R ux, R uy, R uz) {
+    constexpr int NL = Lat<D>::Q / 3;
+    if constexpr (D == 3) {
+#pragma unroll
+        for (int t = 0; t < 9; ++t) fwd1_T(m[t], m[9 + t], m[18 + t], uz);
+    }
+#pragma unroll
+    for (int c = 0; c < Lat<D>::NZ; ++c)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) fwd1_T(m[9 * c + a], m[9 * c + 3 + a], m[9 * c + 6 + a], uy);
+#pragma unroll
+    for (int l = 0; l < NL; ++l) fwd1_T(m[3 * l], m[3 * l + 1], m[3 * l + 2], ux);
+}
+template <int D, class R> __device__ __forceinline__ void inv_T(R (&m)[Lat<D>::Q], R ux, R uy, R uz) {
+    constexpr int NL = Lat<D>::Q / 3;
+#pragma unroll
+    for (int l = 0; l < NL; ++l) inv1_T(m[3 * l], m[3 * l + 1], m[3 * l + 2], ux);
+#pragma unroll
+    for (int c = 0; c < Lat<D>::NZ; ++c)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) inv1_T(m[9 * c + a], m[9 * c + 3 + a], m[9 * c + 6 + a], uy);
+    if constexpr (D == 3) {
+#pragma unroll
+        for (int t = 0; t < 9; ++t) inv1_T(m[t], m[9 + t], m[18 + t], uz);
+    }
+}
+
+// sum_a bar_a * alpha_d(a) * val_(a - e_d) for the three axes
+template <int D, class R>
+__device__ __forceinline__ void shift_contract(const R (&bar)[Lat<D>::Q], const R (&val)[Lat<D>::Q], R out[3]) {
+    constexpr int Q = Lat<D>::Q;
+    R sx = 0, sy = 0, sz = 0;
+#pragma unroll
+    for (int t = 0; t < Q; ++t) {
+        const int a = ex_a(t), b = ex_b(t), c = ex_c(t);
+        if (a > 0) sx += R(a) * bar[t] * val[t > 0 ? t - 1 : 0];
+        if (b > 0) sy += R(b) * bar[t] * val[t > 2 ? t - 3 : 0];
+        if (c > 0) sz += R(c) * bar[t] * val[t > 8 ? t - 9 : 0];
+    }
+    out[0] = sx;
+    out[1] = sy;
+    out[2] = sz;
+}
+
+// Source index of direction i for the pull at (x, y, z): (direction, cell) of the element read.
+template <int D, bool WALLS>
+__device__ __forceinline__ void pull_source(int i, int x, int y, int z, const Params& p, int& dir, unsigned& cell) {
+    int s[3] = {x - Lat<D>::ex(i), y - Lat<D>::ey(i), z - Lat<D>::ez(i)};
+    const int n[3] = {p.nx, p.ny, p.nz};
+    bool out = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (s[a] < 0 || s[a] >= n[a]) {
+            if (!WALLS || p.bc[a] == 0) s[a] += (s[a] < 0) ? n[a] : -n[a];
+            else out = true;
+        }
+    }
+    if (out) {
+        dir = Lat<D>::opp(i);
+        cell = (unsigned)((z * p.ny + y) * p.nx + x);
+    } else {
+        dir = i;
+        cell = (unsigned)((s[2] * p.ny + s[1]) * p.nx + s[0]);
+    }
+}
+
+template <int D, class S, bool WALLS>
+__global__ void __launch_bounds__(kBlock) k_adjoint_terminal(const S* __restrict__ state, const typename Codec<S>::R* __restrict__ Ff,
+                                                            Params p, const double* __restrict__ dLdu,
+                                                            const double* __restrict__ dLdrho,
+                                                            typename Codec<S>::R* __restrict__ lam, double* __restrict__ dLdF) {
+    using R = typename Codec<S>::R;
+    constexpr int Q = Lat<D>::Q;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= p.nx || y >= p.ny) return;
+    const unsigned cell = (unsigned)((z * p.ny + y) * p.nx + x);
+    R h[Q];
+    gather<D, S, WALLS>(state, x, y, z, p, h);
+    R F[3];
+    load_force<R>(Ff, p, cell, F);
+    const Hydro<D, R> hy = hydro<D, R>(h, F, p);
+    const R rho = R(1) + hy.drho, irho = R(1) / rho;
+    const R mu[3] = {(R)dLdu[cell], (R)dLdu[p.N + cell], D == 3 ? (R)dLdu[2 * p.N + cell] : R(0)};
+    const R mr = dLdrho ? (R)dLdrho[cell] : R(0);
+    const R u[3] = {hy.ux, hy.uy, hy.uz};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const R e[3] = {(R)Lat<D>::ex(i), (R)Lat<D>::ey(i), (R)Lat<D>::ez(i)};
+        const R nu = mr + irho * (mu[0] * (e[0] - u[0]) + mu[1] * (e[1] - u[1]) + mu[2] * (e[2] - u[2]));
+        int dir;
+        unsigned sc;
+        pull_source<D, WALLS>(i, x, y, z, p, dir, sc);
+        lam[(long long)dir * p.N + sc] = nu;
+    }
+#pragma unroll
+    for (int d = 0; d < D; ++d) dLdF[d * p.N + cell] += (double)(R(0.5) * mu[d] * irho);
+}
+
+template <int D, class S, bool WALLS>
+__global__ void __launch_bounds__(kBlock) k_adjoint_step(const S* __restrict__ state, const typename Codec<S>::R* __restrict__ Ff,
+                                                        Params p, const typename Codec<S>::R* __restrict__ lam_in,
+                                                        typename Codec<S>::R* __restrict__ lam_out, double* __restrict__ dLdF) {
+    using R = typename Codec<S>::R;
+    constexpr int Q = Lat<D>::Q;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= p.nx || y >= p.ny) return;
+    const unsigned cell = (unsigned)((z * p.ny + y) * p.nx + x);
+
+    // ---- forward recomputation (plain central moments of fbar) ----
+    R A[Q];                                   // pull, then kbar
+    gather<D, S, WALLS>(state, x, y, z, p, A);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) A[slot<D>(i)] += (R)weight<D>(i);
+    R F[3];
+    load_force<R>(Ff, p, cell, F);
+    R rho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int t = 0; t < Q; ++t) {
+        rho += A[t];
+        jx += R(ex_a(t) - 1) * A[t];
+        jy += R(ex_b(t) - 1) * A[t];
+        if constexpr (D == 3) jz += R(ex_c(t) - 1) * A[t];
+    }
+    const R irho = R(1) / rho;
+    const R u[3] = {(jx + R(0.5) * F[0]) * irho, (jy + R(0.5) * F[1]) * irho, D == 3 ? (jz + R(0.5) * F[2]) * irho : R(0)};
+    central_forward<D, R>(A, u[0], u[1], u[2]);      // A = kbar
+
+    const R Fr[3] = {F[0] * irho, F[1] * irho, F[2] * irho};
+    const R wnu = R(1) / (R)p.tau0;
+    const R wb = (p.omega_bulk > 0.0) ? (R)p.omega_bulk : wnu;
+    const R w3 = (R)p.omega3, w4 = (R)p.omega4;
+    const R third = R(1) / 3;
+
+    // kappa of f (orders >= 2) and post-collision central moments B
+    R K[Q];
+    R B[Q];
+#pragma unroll
+    for (int t = 0; t < Q; ++t) K[t] = A[t];
+#pragma unroll
+    for (int n = 3; n <= 2 * D; ++n) {
+#pragma unroll
+        for (int t = 0; t < Q; ++t) {
+            if (ord(t) != n) continue;
+            const int a = ex_a(t), b = ex_b(t), c = ex_c(t);
+            R s = 0;
+            if (a > 0) s += R(a) * Fr[0] * K[t > 0 ? t - 1 : 0];
+            if (b > 0) s += R(b) * Fr[1] * K[t > 2 ? t - 3 : 0];
+            if (c > 0) s += R(c) * Fr[2] * K[t > 8 ? t - 9 : 0];
+            K[t] = A[t] + R(0.5) * s;
+            const bool even = (a % 2 == 0) && (b % 2 == 0) && (c % 2 == 0);
+            const R cM = even ? (R)third_pow((a == 2) + (b == 2) + (c == 2)) : R(0);
+            const R w = (n == 3) ? w3 : w4;
+            B[t] = (R(1) - w) * A[t] + w * cM * rho + (R(1) - R(0.5) * w) * s;
+        }
+    }
+    // order 2: trace with wb, deviator / off-diagonal with wnu
+    {
+        const int dg[3] = {midx(2, 0, 0), midx(0, 2, 0), midx(0, 0, 2)};
+        R P[3] = {0, 0, 0}, tr = 0;
+#pragma unroll
+        for (int d = 0; d < D; ++d) { P[d] = A[dg[d]] - rho * third; tr += P[d]; }
+        const R corr = (wnu - wb) * tr * (R(1) / D);
+#pragma unroll
+        for (int d = 0; d < D; ++d) B[dg[d]] = rho * third + (R(1) - wnu) * P[d] + corr;
+        B[midx(1, 1, 0)] = (R(1) - wnu) * A[midx(1, 1, 0)];
+        if constexpr (D == 3) {
+            B[midx(1, 0, 1)] = (R(1) - wnu) * A[midx(1, 0, 1)];
+            B[midx(0, 1, 1)] = (R(1) - wnu) * A[midx(0, 1, 1)];
+        }
+    }
+    B[0] = A[0];
+    B[midx(1, 0, 0)] = A[midx(1, 0, 0)] + F[0];
+    B[midx(0, 1, 0)] = A[midx(0, 1, 0)] + F[1];
+    if constexpr (D == 3) B[midx(0, 0, 1)] = A[midx(0, 0, 1)] + F[2];
+
+    // ---- reverse ----
+    R L[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) L[slot<D>(i)] = __ldg(lam_in + (long long)i * p.N + cell);
+    inv_T<D, R>(L, u[0], u[1], u[2]);           // L = postbar
+    R ub[3];
+    shift_contract<D, R>(L, B, ub);              // inverse-transform u derivative
+    R rb = 0, Fb[3] = {0, 0, 0};
+
+    // first and zeroth order
+    Fb[0] += L[midx(1, 0, 0)];
+    Fb[1] += L[midx(0, 1, 0)];
+    if constexpr (D == 3) Fb[2] += L[midx(0, 0, 1)];
+
+    // orders >= 3, decreasing; B is reused as kappabar accumulators
+#pragma unroll
+    for (int t = 0; t < Q; ++t) B[t] = R(0);
+#pragma unroll
+    for (int n = 2 * D; n >= 3; --n) {
+#pragma unroll
+        for (int t = 0; t < Q; ++t) {
+            if (ord(t) != n) continue;
+            const int a = ex_a(t), b = ex_b(t), c = ex_c(t);
+            const bool even = (a % 2 == 0) && (b % 2 == 0) && (c % 2 == 0);
+            const R cM = even ? (R)third_pow((a == 2) + (b == 2) + (c == 2)) : R(0);
+            const R w = (n == 3) ? w3 : w4;
+            const R pb = L[t];
+            const R sb = (R(1) - R(0.5) * w) * pb + R(0.5) * B[t];
+            rb += w * cM * pb;
+            L[t] = (R(1) - w) * pb + B[t];       // kbarbar
+            if (a > 0) { const R kv = K[t > 0 ? t - 1 : 0]; Fb[0] += R(a) * kv * irho * sb; rb -= R(a) * Fr[0] * irho * kv * sb; B[t > 0 ? t - 1 : 0] += R(a) * Fr[0] * sb; }
+            if (b > 0) { const R kv = K[t > 2 ? t - 3 : 0]; Fb[1] += R(b) * kv * irho * sb; rb -= R(b) * Fr[1] * irho * kv * sb; B[t > 2 ? t - 3 : 0] += R(b) * Fr[1] * sb; }
+            if (c > 0) { const R kv = K[t > 8 ? t - 9 : 0]; Fb[2] += R(c) * kv * irho * sb; rb -= R(c) * Fr[2] * irho * kv * sb; B[t > 8 ? t - 9 : 0] += R(c) * Fr[2] * sb; }
+        }
+    }
+    // order 2
+    {
+        const int dg[3] = {midx(2, 0, 0), midx(0, 2, 0), midx(0, 0, 2)};
+        R pb[3] = {0, 0, 0}, trb = 0;
+#pragma unroll
+        for (int d = 0; d < D; ++d) { pb[d] = L[dg[d]]; trb += pb[d]; }
+        const R corr = (wnu - wb) * trb * (R(1) / D);   // R is symmetric
+        R sumP = 0;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const R Pb = (R(1) - wnu) * pb[d] + corr;     // bar of P_d
+            L[dg[d]] = Pb + B[dg[d]];
+            sumP += Pb;
+        }
+        rb += third * trb - third * sumP;
+        L[midx(1, 1, 0)] = (R(1) - wnu) * L[midx(1, 1, 0)] + B[midx(1, 1, 0)];
+        if constexpr (D == 3) {
+            L[midx(1, 0, 1)] = (R(1) - wnu) * L[midx(1, 0, 1)] + B[midx(1, 0, 1)];
+            L[midx(0, 1, 1)] = (R(1) - wnu) * L[midx(0, 1, 1)] + B[midx(0, 1, 1)];
+        }
+    }
+    // orders 0 and 1: kbarbar = postbar (identity), already in L
+
+    // forward transform: u derivative and transpose
+    R ub2[3];
+    shift_contract<D, R>(L, A, ub2);
+    ub[0] -= ub2[0];
+    ub[1] -= ub2[1];
+    ub[2] -= ub2[2];
+    fwd_T<D, R>(L, u[0], u[1], u[2]);            // L = gbar (slot order)
+
+    // u = (sum g e + F/2) / rho, rho = sum g
+    const R ue = -(ub[0] * u[0] + ub[1] * u[1] + ub[2] * u[2]) * irho;
+#pragma unroll
+    for (int t = 0; t < Q; ++t) {
+        const R e0 = R(ex_a(t) - 1), e1 = R(ex_b(t) - 1), e2 = R(ex_c(t) - 1);
+        L[t] += rb + ue + irho * (ub[0] * e0 + ub[1] * e1 + (D == 3 ? ub[2] * e2 : R(0)));
+    }
+    Fb[0] += R(0.5) * irho * ub[0];
+    Fb[1] += R(0.5) * irho * ub[1];
+    Fb[2] += R(0.5) * irho * ub[2];
+
+    // scatter through the transpose of the pull
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        int dir;
+        unsigned sc;
+        pull_source<D, WALLS>(i, x, y, z, p, dir, sc);
+        lam_out[(long long)dir * p.N + sc] = L[slot<D>(i)];
+    }
+#pragma unroll
+    for (int d = 0; d < D; ++d) dLdF[d * p.N + cell] += (double)Fb[d];
+}
+
+}  // namespace
+
+template <int D, class R>
+cudaError_t launch_adjoint_terminal(const void* state, const void* Ff, const Params& p, const double* dLdu,
+                                    const double* dLdrho, void* lambda, double* dLdF, cudaStream_t st) {
+    const dim3 b = cell_block(p.nx), g = cell_grid(p, b);
+    if (has_walls(p))
+        k_adjoint_terminal<D, R, true><<<g, b, 0, st>>>((const R*)state, (const R*)Ff, p, dLdu, dLdrho, (R*)lambda, dLdF);
+    else
+        k_adjoint_terminal<D, R, false><<<g, b, 0, st>>>((const R*)state, (const R*)Ff, p, dLdu, dLdrho, (R*)lambda, dLdF);
+    return cudaGetLastError();
+}
+
+template <int D, class R>
+cudaError_t launch_adjoint_step(const void* state, const void* Ff, const Params& p, const void* lam_in, void* lam_out,
+                                double* dLdF, cudaStream_t st) {
+    const dim3 b = cell_block(p.nx), g = cell_grid(p, b);
+    if (has_walls(p))
+        k_adjoint_step<D, R, true><<<g, b, 0, st>>>((const R*)state, (const R*)Ff, p, (const R*)lam_in, (R*)lam_out, dLdF);
+    else
+        k_adjoint_step<D, R, false><<<g, b, 0, st>>>((const R*)state, (const R*)Ff, p, (const R*)lam_in, (R*)lam_out, dLdF);
+    return cudaGetLastError();
+}
+
+#define CM_ADJ(D, R)                                                                                               \
+    template cudaError_t launch_adjoint_terminal<D, R>(const void*, const void*, const Params&, const double*,     \
+                                                       const double*, void*, double*, cudaStream_t);               \
+    template cudaError_t launch_adjoint_step<D, R>(const void*, const void*, const Params&, const void*, void*,     \
+                                                   double*, cudaStream_t);
+CM_ADJ(3, double)
+CM_ADJ(3, float)
+CM_ADJ(2, double)
+CM_ADJ(2, float)
+
 }  // namespace cm

@@ -149,6 +149,8 @@ int cmlbm_create(const cmlbm_config* cfg, cmlbm_t** out) {
     if (c.lattice == CMLBM_D2Q9 && c.nz != 1) return fail(nullptr, CMLBM_ERR_INVALID, "D2Q9 needs nz == 1");
     const long long N = (long long)c.nx * c.ny * c.nz;
     if (N >= (1LL << 31)) return fail(nullptr, CMLBM_ERR_INVALID, "nx*ny*nz must be < 2^31");
+    if (N * (c.lattice == CMLBM_D3Q27 ? 27 : 9) >= (1LL << 32))
+        return fail(nullptr, CMLBM_ERR_INVALID, "Q*nx*ny*nz must be < 2^32 (32-bit element offsets)");
     if (c.nz > 65535) return fail(nullptr, CMLBM_ERR_INVALID, "nz must be <= 65535");
     if (c.ny > 65535) return fail(nullptr, CMLBM_ERR_INVALID, "ny must be <= 65535");
     for (int a = 0; a < 3; ++a)

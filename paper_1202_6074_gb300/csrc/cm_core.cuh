@@ -41,6 +41,13 @@ struct Params {
     double rho0;
 };
 
+// Compile-time features of a kernel variant: walls present, eddy viscosity, per-cell force
+// field, and the less common forms (factorized attractor / reduced compressibility) read from
+// Params at run time.
+template <bool WALLS_, bool LES_, bool FIELD_, bool GEN_> struct Feat {
+    static constexpr bool WALLS = WALLS_, LES = LES_, FIELD = FIELD_, GEN = GEN_;
+};
+
 // ------------------------------------------------------------------------------------------
 // Lattices
 // ------------------------------------------------------------------------------------------
@@ -72,8 +79,21 @@ template <> struct Lat<2> {
 };
 
 template <int D> __host__ __device__ constexpr int slot(int i) {
-    return (Lat<D>::ex(i) + 1) + 3 * (Lat<D>::ey(i) + 1) + 9 * (Lat<D>::ez(i) + 1);
+    return (Lat<D>::ex(i) + 1) + 3 * (Lat<D>::ey(i) + 1) + (D == 3 ? 9 * (Lat<D>::ez(i) + 1) : 0);
 }
+template <int D> constexpr bool slots_valid() {
+    bool seen[27] = {};
+    for (int i = 0; i < Lat<D>::Q; ++i) {
+        const int t = slot<D>(i);
+        if (t < 0 || t >= Lat<D>::Q || seen[t]) return false;
+        seen[t] = true;
+        if (Lat<D>::opp(Lat<D>::opp(i)) != i) return false;
+        if (Lat<D>::ex(Lat<D>::opp(i)) != -Lat<D>::ex(i) || Lat<D>::ey(Lat<D>::opp(i)) != -Lat<D>::ey(i)) return false;
+    }
+    return true;
+}
+static_assert(slots_valid<2>() && slots_valid<3>(), "direction tables");
+
 __host__ __device__ constexpr double w1(int e) { return e == 0 ? 2.0 / 3.0 : 1.0 / 6.0; }
 template <int D> __host__ __device__ constexpr double weight(int i) {
     return w1(Lat<D>::ex(i)) * w1(Lat<D>::ey(i)) * (D == 3 ? w1(Lat<D>::ez(i)) : 1.0);
@@ -147,7 +167,7 @@ __device__ __forceinline__ void gather(const S* __restrict__ src, int x, int y, 
                                        typename Codec<S>::R (&h)[Lat<D>::Q]) {
     using R = typename Codec<S>::R;
     constexpr int Q = Lat<D>::Q;
-    const long long N = p.N;
+    const unsigned N = (unsigned)p.N;       // Q * N < 2^32 is checked at create
     int xs[3], ys[3], zs[3];
     bool xo[3] = {false, false, false}, yo[3] = {false, false, false}, zo[3] = {false, false, false};
 #pragma unroll
@@ -179,7 +199,7 @@ __device__ __forceinline__ void gather(const S* __restrict__ src, int x, int y, 
         const int a = Lat<D>::ex(i) + 1, b = Lat<D>::ey(i) + 1, c = Lat<D>::ez(i) + 1;
         R d;
         if (WALLS && (xo[a] || yo[b] || zo[c])) {
-            d = Codec<S>::ld(src + (long long)Lat<D>::opp(i) * N + cell);
+            d = Codec<S>::ld(src + (Lat<D>::opp(i) * N + cell));
             R wx = 0, wy = 0, wz = 0, cnt = 0;
             // slot 2 (e = +1) crosses the lower wall (side 0), slot 0 (e = -1) the upper (side 1)
             if (xo[a]) { const int s = (a == 2) ? 0 : 1; wx += (R)p.uw[0][s][0]; wy += (R)p.uw[0][s][1]; wz += (R)p.uw[0][s][2]; cnt += 1; }
@@ -189,7 +209,7 @@ __device__ __forceinline__ void gather(const S* __restrict__ src, int x, int y, 
             d += R(6) * eu / cnt;
         } else {
             const unsigned sc = (unsigned)((zs[c] * p.ny + ys[b]) * p.nx + xs[a]);
-            d = Codec<S>::ld(src + (long long)i * N + sc);
+            d = Codec<S>::ld(src + (i * N + sc));
         }
         h[slot<D>(i)] = d * (R)weight<D>(i);
     }
@@ -202,7 +222,7 @@ template <int D, class R> struct Hydro {
     R drho, jx, jy, jz, ux, uy, uz;
 };
 
-template <int D, class R>
+template <int D, class R, bool GEN = true>
 __device__ __forceinline__ Hydro<D, R> hydro(const R (&h)[Lat<D>::Q], const R F[3], const Params& p) {
     constexpr int NL = Lat<D>::Q / 3;
     Hydro<D, R> o;
@@ -224,7 +244,7 @@ __device__ __forceinline__ Hydro<D, R> hydro(const R (&h)[Lat<D>::Q], const R F[
     o.jx = jx + R(0.5) * F[0];
     o.jy = jy + R(0.5) * F[1];
     o.jz = jz + R(0.5) * F[2];
-    const R inv = R(1) / (p.reduced ? (R)p.rho0 : R(1) + drho);
+    const R inv = R(1) / ((GEN && p.reduced) ? (R)p.rho0 : R(1) + drho);
     o.ux = o.jx * inv;
     o.uy = o.jy * inv;
     o.uz = (D == 3) ? o.jz * inv : R(0);
@@ -277,10 +297,10 @@ template <class R> __device__ __forceinline__ R excess(const R* q, bool x, bool 
 // In: h deviation populations (slot order), force F, the eddy-viscosity constant cs_eff (0 = off).
 // Out: h holds the post-collision deviation populations.
 // ------------------------------------------------------------------------------------------
-template <int D, class R>
+template <int D, class R, class FT>
 __device__ __forceinline__ void collide(R (&m)[Lat<D>::Q], const R F[3], const Params& p, R cs_eff) {
     constexpr int Q = Lat<D>::Q;
-    const Hydro<D, R> hy = hydro<D, R>(m, F, p);
+    const Hydro<D, R> hy = hydro<D, R, FT::GEN>(m, F, p);
     const R drho = hy.drho, rho = R(1) + hy.drho;
     const R u[3] = {hy.ux, hy.uy, hy.uz};
     central_forward<D, R>(m, u[0], u[1], u[2]);
@@ -305,7 +325,7 @@ __device__ __forceinline__ void collide(R (&m)[Lat<D>::Q], const R F[3], const P
     }
 
     R tau = (R)p.tau0;
-    if (cs_eff > R(0)) {
+    if (FT::LES && cs_eff > R(0)) {
         const R Qn = sqrt(Pxx * Pxx + Pyy * Pyy + Pzz * Pzz + R(2) * (Pxy * Pxy + Pxz * Pxz + Pyz * Pyz));
         tau = R(0.5) * (tau + sqrt(tau * tau + R(25.455844122715710878) * cs_eff * cs_eff * Qn * irho));
     }
@@ -351,7 +371,7 @@ __device__ __forceinline__ void collide(R (&m)[Lat<D>::Q], const R F[3], const P
             const bool even = (a % 2 == 0) && (b % 2 == 0) && (c % 2 == 0);
             const int twos = (a == 2) + (b == 2) + (c == 2);
             R DM;
-            if (p.attractor == 0) {
+            if (!FT::GEN || p.attractor == 0) {
                 DM = even ? drho * (R)third_pow(twos) - excess(q, a == 2, b == 2, c == 2) : -kw;
             } else {
                 // factorized attractor (Sec. 11): products of relaxed second-order moments / rho^(k-1)

@@ -7,6 +7,10 @@ namespace cm {
 
 // Threads per block of the cell kernels and the block shape for a given nx.
 constexpr int kBlock = 128;
+// Minimum resident blocks per SM requested from the register allocator for the step kernel.
+#ifndef CM_STEP_MIN_BLOCKS
+#define CM_STEP_MIN_BLOCKS 1
+#endif
 inline dim3 cell_block(int nx) {
     int bx = 32;
     while (bx < kBlock && bx < nx) bx *= 2;
@@ -16,12 +20,13 @@ inline dim3 cell_grid(const Params& p, dim3 b) {
     return dim3((p.nx + b.x - 1) / b.x, (p.ny + b.y - 1) / b.y, p.nz);
 }
 
-template <class R>
+template <class R, bool FIELD = true>
 __device__ __forceinline__ void load_force(const R* __restrict__ Ff, const Params& p, unsigned cell, R F[3]) {
-    if (p.has_field) {
+    if (FIELD && p.has_field) {
+        const unsigned N = (unsigned)p.N;
         F[0] = __ldg(Ff + cell);
-        F[1] = __ldg(Ff + p.N + cell);
-        F[2] = __ldg(Ff + 2 * p.N + cell);
+        F[1] = __ldg(Ff + (N + cell));
+        F[2] = __ldg(Ff + (2 * N + cell));
     } else {
         F[0] = (R)p.F[0];
         F[1] = (R)p.F[1];
@@ -29,9 +34,9 @@ __device__ __forceinline__ void load_force(const R* __restrict__ Ff, const Param
     }
 }
 
-template <class R>
+template <class R, bool LES = true>
 __device__ __forceinline__ R smagorinsky_constant(const Params& p, int y) {
-    if (!p.les) return R(0);
+    if (!LES || !p.les) return R(0);
     R c = (R)p.cs;
     if (p.vd) {
         const R yw = fmin((R)y + R(0.5), (R)p.ny - R(0.5) - (R)y);
@@ -41,8 +46,8 @@ __device__ __forceinline__ R smagorinsky_constant(const Params& p, int y) {
 }
 
 // ---- fused pull + collide + store --------------------------------------------------------
-template <int D, class S, bool WALLS>
-__global__ void __launch_bounds__(kBlock) k_step(const S* __restrict__ src, S* __restrict__ dst,
+template <int D, class S, class FT>
+__global__ void __launch_bounds__(kBlock, CM_STEP_MIN_BLOCKS) k_step(const S* __restrict__ src, S* __restrict__ dst,
                                                 const typename Codec<S>::R* __restrict__ Ff, Params p) {
     using R = typename Codec<S>::R;
     constexpr int Q = Lat<D>::Q;
@@ -51,14 +56,14 @@ __global__ void __launch_bounds__(kBlock) k_step(const S* __restrict__ src, S* _
     const int z = blockIdx.z;
     if (x >= p.nx || y >= p.ny) return;
     const unsigned cell = (unsigned)((z * p.ny + y) * p.nx + x);
+    const unsigned N = (unsigned)p.N;
     R h[Q];
-    gather<D, S, WALLS>(src, x, y, z, p, h);
+    gather<D, S, FT::WALLS>(src, x, y, z, p, h);
     R F[3];
-    load_force<R>(Ff, p, cell, F);
-    collide<D, R>(h, F, p, smagorinsky_constant<R>(p, y));
+    load_force<R, FT::FIELD>(Ff, p, cell, F);
+    collide<D, R, FT>(h, F, p, smagorinsky_constant<R, FT::LES>(p, y));
 #pragma unroll
-    for (int i = 0; i < Q; ++i)
-        Codec<S>::st(dst + (long long)i * p.N + cell, h[slot<D>(i)] * (R)inv_weight<D>(i));
+    for (int i = 0; i < Q; ++i) Codec<S>::st(dst + (i * N + cell), h[slot<D>(i)] * (R)inv_weight<D>(i));
 }
 
 // ---- density and velocity of the pulled field ----------------------------------------------
@@ -251,14 +256,33 @@ __global__ void k_convert_force(const double* __restrict__ in, R* __restrict__ o
 // ------------------------------------------------------------------------------------------
 inline bool has_walls(const Params& p) { return p.bc[0] || p.bc[1] || p.bc[2]; }
 
-template <int D, class S>
-cudaError_t launch_step(const void* src, void* dst, const void* Ff, const Params& p, cudaStream_t st) {
+template <int D, class S, class FT>
+void launch_step_ft(const void* src, void* dst, const void* Ff, const Params& p, cudaStream_t st) {
     using R = typename Codec<S>::R;
     const dim3 b = cell_block(p.nx), g = cell_grid(p, b);
-    if (has_walls(p))
-        k_step<D, S, true><<<g, b, 0, st>>>((const S*)src, (S*)dst, (const R*)Ff, p);
-    else
-        k_step<D, S, false><<<g, b, 0, st>>>((const S*)src, (S*)dst, (const R*)Ff, p);
+    k_step<D, S, FT><<<g, b, 0, st>>>((const S*)src, (S*)dst, (const R*)Ff, p);
+}
+
+template <int D, class S, bool W, bool L, bool F>
+void launch_step_g(const void* src, void* dst, const void* Ff, const Params& p, cudaStream_t st) {
+    if (p.attractor != 0 || p.reduced) launch_step_ft<D, S, Feat<W, L, F, true>>(src, dst, Ff, p, st);
+    else launch_step_ft<D, S, Feat<W, L, F, false>>(src, dst, Ff, p, st);
+}
+template <int D, class S, bool W, bool L>
+void launch_step_f(const void* src, void* dst, const void* Ff, const Params& p, cudaStream_t st) {
+    if (p.has_field) launch_step_g<D, S, W, L, true>(src, dst, Ff, p, st);
+    else launch_step_g<D, S, W, L, false>(src, dst, Ff, p, st);
+}
+template <int D, class S, bool W>
+void launch_step_l(const void* src, void* dst, const void* Ff, const Params& p, cudaStream_t st) {
+    if (p.les) launch_step_f<D, S, W, true>(src, dst, Ff, p, st);
+    else launch_step_f<D, S, W, false>(src, dst, Ff, p, st);
+}
+
+template <int D, class S>
+cudaError_t launch_step(const void* src, void* dst, const void* Ff, const Params& p, cudaStream_t st) {
+    if (has_walls(p)) launch_step_l<D, S, true>(src, dst, Ff, p, st);
+    else launch_step_l<D, S, false>(src, dst, Ff, p, st);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,108 @@
+"""Differentiable rollout: dL/dF of a loss on the final velocity, by the hand-written adjoint.
+
+``velocity_after(solver, F, s0, steps, segment)`` returns u_T ([3, nz, ny, nx], float64) after
+``steps`` stream-and-collide steps from the fixed state ``s0`` under the force field F, as a
+torch.autograd.Function. Its backward runs the adjoint kernels of libcmlbm.so:
+
+  forward   s_{t+1} = step(s_t, F); a checkpoint is kept every ``segment`` steps
+  backward  lambda_T = pull^T (du_T/dg)^T dL/du_T           (cmlbm_adjoint_terminal)
+            for each segment, last first: recompute its states from the checkpoint
+            (cmlbm_step_buffers), then lambda_t = J_t^T lambda_{t+1} and dL/dF += ...
+            (cmlbm_step_adjoint), with dL/dF accumulated in FP64.
+Memory: ceil(steps / segment) checkpoints plus one segment of states, instead of all steps.
+The initial state s0 is an input held fixed (its own dependence on F is not differentiated).
+"""
+import time
+
+import torch
+
+from . import cmlbm as _cm
+
+
+class _Rollout(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, F, solver, s0, steps, segment):
+        solver.set_force((0.0, 0.0, 0.0), F.detach())
+        ckpts = [s0.detach().clone()]
+        cur = s0.detach().clone()
+        nxt = solver.new_state()
+        for t in range(steps):
+            solver.step_buffers(cur, nxt)
+            cur, nxt = nxt, cur
+            if (t + 1) % segment == 0 and t + 1 < steps:
+                ckpts.append(cur.clone())
+        _, u = solver.moments(state=cur)
+        ctx.solver, ctx.steps, ctx.segment = solver, steps, segment
+        ctx.ckpts = ckpts
+        ctx.final = cur
+        ctx.F = F.detach()
+        return u
+
+    @staticmethod
+    def backward(ctx, gu):
+        solver, steps, segment = ctx.solver, ctx.steps, ctx.segment
+        solver.set_force((0.0, 0.0, 0.0), ctx.F)
+        dev = solver.device
+        shape = (solver.Q,) + solver.shape
+        lam = torch.empty(shape, dtype=solver.real_dtype, device=dev)
+        lam2 = torch.empty_like(lam)
+        dLdF = torch.zeros((3,) + solver.shape, dtype=torch.float64, device=dev)
+        solver.adjoint_terminal(ctx.final, gu.detach().to(torch.float64).contiguous(), lam, dLdF)
+        nseg = (steps + segment - 1) // segment
+        buf = [None] * segment
+        for k in reversed(range(nseg)):
+            start, end = k * segment, min((k + 1) * segment, steps)
+            buf[0] = ctx.ckpts[k]
+            for t in range(start + 1, end):
+                j = t - start
+                if buf[j] is None or buf[j] is buf[0]:
+                    buf[j] = solver.new_state()
+                solver.step_buffers(buf[j - 1], buf[j])
+            for t in reversed(range(start, end)):
+                solver.step_adjoint(buf[t - start], lam, lam2, dLdF)
+                lam, lam2 = lam2, lam
+        return dLdF, None, None, None, None
+
+
+def velocity_after(solver, F, s0, steps, segment=50):
+    """u_T (float64 CUDA tensor [3, nz, ny, nx]) as a differentiable function of F."""
+    if steps < 1:
+        raise ValueError("steps must be >= 1")
+    return _Rollout.apply(F, solver, s0, int(steps), int(max(1, segment)))
+
+
+def benchmark(cm, n=128, steps=100, segment=50):
+    """Forward rollout and its adjoint on the n^3 adjoint workload (FP32 storage)."""
+    from . import workloads as W
+
+    s = cm.Solver(lattice="D3Q27", nx=n, ny=n, nz=n, storage="f32", tau=0.6)
+    rho, u0 = W.random_solenoidal(n, n, n, seed=2, u_rms=0.02)
+    F = torch.tensor(W.gaussian_force(n, n, n, seed=3, std=1e-5), device="cuda")
+    s.set_force((0, 0, 0), F)
+    s.init(torch.tensor(rho, device="cuda"), torch.tensor(u0, device="cuda"))
+    s0 = s.get_state()
+    target = torch.zeros((3, n, n, n), dtype=torch.float64, device="cuda")
+    Fp = F.clone().requires_grad_(True)
+    # warm-up
+    u = velocity_after(s, Fp, s0, 2, 1)
+    ((u - target) ** 2).sum(0).mean().backward()
+    torch.cuda.synchronize()
+    Fp.grad = None
+    l0 = s.launch_count
+    t0 = time.perf_counter()
+    u = velocity_after(s, Fp, s0, steps, segment)
+    loss = ((u - target) ** 2).sum(0).mean()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    loss.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    N = n ** 3
+    out = {"forward_MLUPS": N * steps / (t1 - t0) / 1e6, "backward_MLUPS": N * steps / (t2 - t1) / 1e6,
+           "fwd_plus_adjoint_MLUPS": N * steps / (t2 - t0) / 1e6, "steps": steps, "segment": segment,
+           "launches": s.launch_count - l0, "grad_norm": float(Fp.grad.norm())}
+    s.close()
+    return out
+
+
+__all__ = ["velocity_after", "benchmark", "_cm"]
