@@ -80,8 +80,8 @@ __device__ __forceinline__ void shift_contract(const R (&bar)[Lat<D>::Q], const 
 }
 
 // Source index of direction i for the pull at (x, y, z): (direction, cell) of the element read.
-template <int D, bool WALLS>
-__device__ __forceinline__ void pull_source(int i, int x, int y, int z, const Params& p, int& dir, unsigned& cell) {
+template <int D, bool WALLS, class R>
+__device__ __forceinline__ void pull_source(int i, int x, int y, int z, const PR<R>& p, int& dir, unsigned& cell) {
     int s[3] = {x - Lat<D>::ex(i), y - Lat<D>::ey(i), z - Lat<D>::ez(i)};
     const int n[3] = {p.nx, p.ny, p.nz};
     bool out = false;
@@ -103,7 +103,7 @@ __device__ __forceinline__ void pull_source(int i, int x, int y, int z, const Pa
 
 template <int D, class S, bool WALLS>
 __global__ void __launch_bounds__(kBlock) k_adjoint_terminal(const S* __restrict__ state, const typename Codec<S>::R* __restrict__ Ff,
-                                                            Params p, const double* __restrict__ dLdu,
+                                                            PR<typename Codec<S>::R> p, const double* __restrict__ dLdu,
                                                             const double* __restrict__ dLdrho,
                                                             typename Codec<S>::R* __restrict__ lam, double* __restrict__ dLdF) {
     using R = typename Codec<S>::R;
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_terminal(const S* __restrict
     R F[3];
     load_force<R>(Ff, p, cell, F);
     const Hydro<D, R> hy = hydro<D, R>(h, F, p);
-    const R rho = R(1) + hy.drho, irho = R(1) / rho;
+    const R rho = R(1) + hy.drho, irho = rcp(rho);
     const R mu[3] = {(R)dLdu[cell], (R)dLdu[p.N + cell], D == 3 ? (R)dLdu[2 * p.N + cell] : R(0)};
     const R mr = dLdrho ? (R)dLdrho[cell] : R(0);
     const R u[3] = {hy.ux, hy.uy, hy.uz};
@@ -128,8 +128,8 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_terminal(const S* __restrict
         const R nu = mr + irho * (mu[0] * (e[0] - u[0]) + mu[1] * (e[1] - u[1]) + mu[2] * (e[2] - u[2]));
         int dir;
         unsigned sc;
-        pull_source<D, WALLS>(i, x, y, z, p, dir, sc);
-        lam[(long long)dir * p.N + sc] = nu;
+        pull_source<D, WALLS, R>(i, x, y, z, p, dir, sc);
+        lam[(unsigned)dir * p.N + sc] = nu;
     }
 #pragma unroll
     for (int d = 0; d < D; ++d) dLdF[d * p.N + cell] += (double)(R(0.5) * mu[d] * irho);
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_terminal(const S* __restrict
 
 template <int D, class S, bool WALLS>
 __global__ void __launch_bounds__(kBlock) k_adjoint_step(const S* __restrict__ state, const typename Codec<S>::R* __restrict__ Ff,
-                                                        Params p, const typename Codec<S>::R* __restrict__ lam_in,
+                                                        PR<typename Codec<S>::R> p, const typename Codec<S>::R* __restrict__ lam_in,
                                                         typename Codec<S>::R* __restrict__ lam_out, double* __restrict__ dLdF) {
     using R = typename Codec<S>::R;
     constexpr int Q = Lat<D>::Q;
@@ -150,8 +150,11 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(const S* __restrict__ s
     // ---- forward recomputation (plain central moments of fbar) ----
     R A[Q];                                   // pull, then kbar
     gather<D, S, WALLS>(state, x, y, z, p, A);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) A[slot<D>(i)] += (R)weight<D>(i);
+    sfor<Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr R w = (R)weight<D>(i);
+        A[slot<D>(i)] += w;
+    });
     R F[3];
     load_force<R>(Ff, p, cell, F);
     R rho = 0, jx = 0, jy = 0, jz = 0;
@@ -162,14 +165,14 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(const S* __restrict__ s
         jy += R(ex_b(t) - 1) * A[t];
         if constexpr (D == 3) jz += R(ex_c(t) - 1) * A[t];
     }
-    const R irho = R(1) / rho;
+    const R irho = rcp(rho);
     const R u[3] = {(jx + R(0.5) * F[0]) * irho, (jy + R(0.5) * F[1]) * irho, D == 3 ? (jz + R(0.5) * F[2]) * irho : R(0)};
     central_forward<D, R>(A, u[0], u[1], u[2]);      // A = kbar
 
     const R Fr[3] = {F[0] * irho, F[1] * irho, F[2] * irho};
-    const R wnu = R(1) / (R)p.tau0;
-    const R wb = (p.omega_bulk > 0.0) ? (R)p.omega_bulk : wnu;
-    const R w3 = (R)p.omega3, w4 = (R)p.omega4;
+    const R wnu = rcp(p.tau0);
+    const R wb = (p.omega_bulk > R(0)) ? p.omega_bulk : wnu;
+    const R w3 = p.omega3, w4 = p.omega4;
     const R third = R(1) / 3;
 
     // kappa of f (orders >= 2) and post-collision central moments B
@@ -177,23 +180,24 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(const S* __restrict__ s
     R B[Q];
 #pragma unroll
     for (int t = 0; t < Q; ++t) K[t] = A[t];
-#pragma unroll
-    for (int n = 3; n <= 2 * D; ++n) {
-#pragma unroll
-        for (int t = 0; t < Q; ++t) {
-            if (ord(t) != n) continue;
-            const int a = ex_a(t), b = ex_b(t), c = ex_c(t);
-            R s = 0;
-            if (a > 0) s += R(a) * Fr[0] * K[t > 0 ? t - 1 : 0];
-            if (b > 0) s += R(b) * Fr[1] * K[t > 2 ? t - 3 : 0];
-            if (c > 0) s += R(c) * Fr[2] * K[t > 8 ? t - 9 : 0];
-            K[t] = A[t] + R(0.5) * s;
-            const bool even = (a % 2 == 0) && (b % 2 == 0) && (c % 2 == 0);
-            const R cM = even ? (R)third_pow((a == 2) + (b == 2) + (c == 2)) : R(0);
-            const R w = (n == 3) ? w3 : w4;
-            B[t] = (R(1) - w) * A[t] + w * cM * rho + (R(1) - R(0.5) * w) * s;
-        }
-    }
+    sfor<2 * D + 1>([&](auto NI) {
+        constexpr int n = decltype(NI)::value;
+        sfor<Q>([&](auto TI) {
+            constexpr int t = decltype(TI)::value;
+            if constexpr (n >= 3 && ord(t) == n) {
+                constexpr int a = ex_a(t), b = ex_b(t), c = ex_c(t);
+                R s = 0;
+                if constexpr (a > 0) s += R(a) * Fr[0] * K[t - 1];
+                if constexpr (b > 0) s += R(b) * Fr[1] * K[t - 3];
+                if constexpr (c > 0) s += R(c) * Fr[2] * K[t - 9];
+                K[t] = A[t] + R(0.5) * s;
+                constexpr bool even = (a % 2 == 0) && (b % 2 == 0) && (c % 2 == 0);
+                constexpr R cM = even ? (R)third_pow((a == 2) + (b == 2) + (c == 2)) : R(0);
+                const R w = (n == 3) ? w3 : w4;
+                B[t] = (R(1) - w) * A[t] + w * cM * rho + (R(1) - R(0.5) * w) * s;
+            }
+        });
+    });
     // order 2: trace with wb, deviator / off-diagonal with wnu
     {
         const int dg[3] = {midx(2, 0, 0), midx(0, 2, 0), midx(0, 0, 2)};
@@ -231,24 +235,25 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(const S* __restrict__ s
     // orders >= 3, decreasing; B is reused as kappabar accumulators
 #pragma unroll
     for (int t = 0; t < Q; ++t) B[t] = R(0);
-#pragma unroll
-    for (int n = 2 * D; n >= 3; --n) {
-#pragma unroll
-        for (int t = 0; t < Q; ++t) {
-            if (ord(t) != n) continue;
-            const int a = ex_a(t), b = ex_b(t), c = ex_c(t);
-            const bool even = (a % 2 == 0) && (b % 2 == 0) && (c % 2 == 0);
-            const R cM = even ? (R)third_pow((a == 2) + (b == 2) + (c == 2)) : R(0);
-            const R w = (n == 3) ? w3 : w4;
-            const R pb = L[t];
-            const R sb = (R(1) - R(0.5) * w) * pb + R(0.5) * B[t];
-            rb += w * cM * pb;
-            L[t] = (R(1) - w) * pb + B[t];       // kbarbar
-            if (a > 0) { const R kv = K[t > 0 ? t - 1 : 0]; Fb[0] += R(a) * kv * irho * sb; rb -= R(a) * Fr[0] * irho * kv * sb; B[t > 0 ? t - 1 : 0] += R(a) * Fr[0] * sb; }
-            if (b > 0) { const R kv = K[t > 2 ? t - 3 : 0]; Fb[1] += R(b) * kv * irho * sb; rb -= R(b) * Fr[1] * irho * kv * sb; B[t > 2 ? t - 3 : 0] += R(b) * Fr[1] * sb; }
-            if (c > 0) { const R kv = K[t > 8 ? t - 9 : 0]; Fb[2] += R(c) * kv * irho * sb; rb -= R(c) * Fr[2] * irho * kv * sb; B[t > 8 ? t - 9 : 0] += R(c) * Fr[2] * sb; }
-        }
-    }
+    sfor<2 * D + 1>([&](auto NI) {
+        constexpr int n = 2 * D - decltype(NI)::value;
+        sfor<Q>([&](auto TI) {
+            constexpr int t = decltype(TI)::value;
+            if constexpr (n >= 3 && ord(t) == n) {
+                constexpr int a = ex_a(t), b = ex_b(t), c = ex_c(t);
+                constexpr bool even = (a % 2 == 0) && (b % 2 == 0) && (c % 2 == 0);
+                constexpr R cM = even ? (R)third_pow((a == 2) + (b == 2) + (c == 2)) : R(0);
+                const R w = (n == 3) ? w3 : w4;
+                const R pb = L[t];
+                const R sb = (R(1) - R(0.5) * w) * pb + R(0.5) * B[t];
+                rb += w * cM * pb;
+                L[t] = (R(1) - w) * pb + B[t];       // kbarbar
+                if constexpr (a > 0) { const R kv = K[t - 1]; Fb[0] += R(a) * kv * irho * sb; rb -= R(a) * Fr[0] * irho * kv * sb; B[t - 1] += R(a) * Fr[0] * sb; }
+                if constexpr (b > 0) { const R kv = K[t - 3]; Fb[1] += R(b) * kv * irho * sb; rb -= R(b) * Fr[1] * irho * kv * sb; B[t - 3] += R(b) * Fr[1] * sb; }
+                if constexpr (c > 0) { const R kv = K[t - 9]; Fb[2] += R(c) * kv * irho * sb; rb -= R(c) * Fr[2] * irho * kv * sb; B[t - 9] += R(c) * Fr[2] * sb; }
+            }
+        });
+    });
     // order 2
     {
         const int dg[3] = {midx(2, 0, 0), midx(0, 2, 0), midx(0, 0, 2)};
@@ -296,8 +301,8 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(const S* __restrict__ s
     for (int i = 0; i < Q; ++i) {
         int dir;
         unsigned sc;
-        pull_source<D, WALLS>(i, x, y, z, p, dir, sc);
-        lam_out[(long long)dir * p.N + sc] = L[slot<D>(i)];
+        pull_source<D, WALLS, R>(i, x, y, z, p, dir, sc);
+        lam_out[(unsigned)dir * p.N + sc] = L[slot<D>(i)];
     }
 #pragma unroll
     for (int d = 0; d < D; ++d) dLdF[d * p.N + cell] += (double)Fb[d];
@@ -310,9 +315,9 @@ cudaError_t launch_adjoint_terminal(const void* state, const void* Ff, const Par
                                     const double* dLdrho, void* lambda, double* dLdF, cudaStream_t st) {
     const dim3 b = cell_block(p.nx), g = cell_grid(p, b);
     if (has_walls(p))
-        k_adjoint_terminal<D, R, true><<<g, b, 0, st>>>((const R*)state, (const R*)Ff, p, dLdu, dLdrho, (R*)lambda, dLdF);
+        k_adjoint_terminal<D, R, true><<<g, b, 0, st>>>((const R*)state, (const R*)Ff, typed<R>(p), dLdu, dLdrho, (R*)lambda, dLdF);
     else
-        k_adjoint_terminal<D, R, false><<<g, b, 0, st>>>((const R*)state, (const R*)Ff, p, dLdu, dLdrho, (R*)lambda, dLdF);
+        k_adjoint_terminal<D, R, false><<<g, b, 0, st>>>((const R*)state, (const R*)Ff, typed<R>(p), dLdu, dLdrho, (R*)lambda, dLdF);
     return cudaGetLastError();
 }
 
@@ -321,9 +326,9 @@ cudaError_t launch_adjoint_step(const void* state, const void* Ff, const Params&
                                 double* dLdF, cudaStream_t st) {
     const dim3 b = cell_block(p.nx), g = cell_grid(p, b);
     if (has_walls(p))
-        k_adjoint_step<D, R, true><<<g, b, 0, st>>>((const R*)state, (const R*)Ff, p, (const R*)lam_in, (R*)lam_out, dLdF);
+        k_adjoint_step<D, R, true><<<g, b, 0, st>>>((const R*)state, (const R*)Ff, typed<R>(p), (const R*)lam_in, (R*)lam_out, dLdF);
     else
-        k_adjoint_step<D, R, false><<<g, b, 0, st>>>((const R*)state, (const R*)Ff, p, (const R*)lam_in, (R*)lam_out, dLdF);
+        k_adjoint_step<D, R, false><<<g, b, 0, st>>>((const R*)state, (const R*)Ff, typed<R>(p), (const R*)lam_in, (R*)lam_out, dLdF);
     return cudaGetLastError();
 }
 

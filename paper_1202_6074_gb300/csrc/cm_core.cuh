@@ -17,7 +17,19 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace cm {
+
+// Compile-time loop: f(std::integral_constant<int, I>) for I = 0 .. N-1, so that table lookups
+// on I (weights, exponents, slots) are constants of the generated code.
+template <class F, int... Is>
+__host__ __device__ __forceinline__ void sfor_impl(F&& f, std::integer_sequence<int, Is...>) {
+    (f(std::integral_constant<int, Is>{}), ...);
+}
+template <int N, class F> __host__ __device__ __forceinline__ void sfor(F&& f) {
+    sfor_impl(f, std::make_integer_sequence<int, N>{});
+}
 
 // ------------------------------------------------------------------------------------------
 // Parameters (plain data, passed by value to every kernel)
@@ -40,6 +52,37 @@ struct Params {
     double vd_aplus, vd_utau_nu;
     double rho0;
 };
+
+// The same parameters in the arithmetic type R (converted once on the host, so kernels do no
+// double-precision work on GB300's narrow FP64 path).
+template <class R> struct PR {
+    int nx, ny, nz;
+    int bc[3];
+    int les, vd, attractor, reduced, has_field;
+    unsigned N;
+    R uw[3][2][3];
+    R F[3];
+    R tau0, omega_bulk, omega3, omega4, cs, vd_aplus, vd_utau_nu, rho0;
+};
+
+template <class R> inline PR<R> typed(const Params& p) {
+    PR<R> q;
+    q.nx = p.nx; q.ny = p.ny; q.nz = p.nz;
+    for (int a = 0; a < 3; ++a) q.bc[a] = p.bc[a];
+    q.les = p.les; q.vd = p.vd; q.attractor = p.attractor; q.reduced = p.reduced; q.has_field = p.has_field;
+    q.N = (unsigned)p.N;
+    for (int a = 0; a < 3; ++a)
+        for (int s = 0; s < 2; ++s)
+            for (int d = 0; d < 3; ++d) q.uw[a][s][d] = (R)p.uw[a][s][d];
+    for (int d = 0; d < 3; ++d) q.F[d] = (R)p.F[d];
+    q.tau0 = (R)p.tau0; q.omega_bulk = (R)p.omega_bulk; q.omega3 = (R)p.omega3; q.omega4 = (R)p.omega4;
+    q.cs = (R)p.cs; q.vd_aplus = (R)p.vd_aplus; q.vd_utau_nu = (R)p.vd_utau_nu; q.rho0 = (R)p.rho0;
+    return q;
+}
+
+// reciprocal: IEEE-rounded intrinsic in FP32, plain division in FP64
+__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 
 // Compile-time features of a kernel variant: walls present, eddy viscosity, per-cell force
 // field, and the less common forms (factorized attractor / reduced compressibility) read from
@@ -105,7 +148,7 @@ __host__ __device__ constexpr int ex_a(int t) { return t % 3; }
 __host__ __device__ constexpr int ex_b(int t) { return (t / 3) % 3; }
 __host__ __device__ constexpr int ex_c(int t) { return t / 9; }
 __host__ __device__ constexpr int midx(int a, int b, int c) { return a + 3 * b + 9 * c; }
-__host__ __device__ constexpr double third_pow(int n) { return n == 0 ? 1.0 : third_pow(n - 1) / 3.0; }
+__host__ __device__ constexpr double third_pow(int n) { return n == 0 ? 1.0 : n == 1 ? 1.0 / 3.0 : n == 2 ? 1.0 / 9.0 : 1.0 / 27.0; }
 
 // ------------------------------------------------------------------------------------------
 // Storage codec: d = fbar / w - 1 stored as S; arithmetic type R
@@ -139,35 +182,35 @@ template <> struct Codec<__half> {
 // ------------------------------------------------------------------------------------------
 // One-dimensional central-moment transforms on (e = -1, 0, +1) populations
 // ------------------------------------------------------------------------------------------
-// forward: (f-, f0, f+) -> (m0, m1, m2) with m_k = sum f (e - u)^k
-template <class R> __device__ __forceinline__ void fwd1(R& a, R& b, R& c, R u) {
-    R m0 = a + b + c;
-    R s1 = c - a;
-    R s2 = c + a;
-    R m1 = s1 - u * m0;
+// forward: (f-, f0, f+) -> (m0, m1, m2) with m_k = sum f (e - u)^k; u2 = u*u, tu = 2u
+template <class R> __device__ __forceinline__ void fwd1(R& a, R& b, R& c, R u, R tu, R u2) {
+    const R m0 = a + b + c;
+    const R s1 = c - a;
+    const R s2 = c + a;
     a = m0;
-    b = m1;
-    c = s2 - u * (s1 + m1);
+    b = s1 - u * m0;
+    c = fma(u2, m0, s2 - tu * s1);
 }
 // inverse: (m0, m1, m2) -> (f-, f0, f+)
-template <class R> __device__ __forceinline__ void inv1(R& a, R& b, R& c, R u) {
-    R m0 = a, m1 = b, m2 = c;
-    R r1 = m1 + u * m0;
-    R r2 = m2 + u * (m1 + r1);
-    a = R(0.5) * (r2 - r1);
+template <class R> __device__ __forceinline__ void inv1(R& a, R& b, R& c, R u, R tu, R u2) {
+    const R m0 = a, m1 = b, m2 = c;
+    const R r1 = fma(u, m0, m1);                  // sum f e
+    const R r2 = fma(u2, m0, fma(tu, m1, m2));    // sum f e^2
+    const R h2 = R(0.5) * r2;
+    const R h1 = R(0.5) * r1;
+    a = h2 - h1;
     b = m0 - r2;
-    c = R(0.5) * (r2 + r1);
+    c = h2 + h1;
 }
 
 // ------------------------------------------------------------------------------------------
 // Pull with periodic wrap and half-way bounce-back; fills h (deviation populations, slot order)
 // ------------------------------------------------------------------------------------------
 template <int D, class S, bool WALLS>
-__device__ __forceinline__ void gather(const S* __restrict__ src, int x, int y, int z, const Params& p,
+__device__ __forceinline__ void gather(const S* __restrict__ src, int x, int y, int z, const PR<typename Codec<S>::R>& p,
                                        typename Codec<S>::R (&h)[Lat<D>::Q]) {
     using R = typename Codec<S>::R;
-    constexpr int Q = Lat<D>::Q;
-    const unsigned N = (unsigned)p.N;       // Q * N < 2^32 is checked at create
+    const unsigned N = p.N;                  // Q * N < 2^32 is checked at create
     int xs[3], ys[3], zs[3];
     bool xo[3] = {false, false, false}, yo[3] = {false, false, false}, zo[3] = {false, false, false};
 #pragma unroll
@@ -194,25 +237,30 @@ __device__ __forceinline__ void gather(const S* __restrict__ src, int x, int y, 
         zs[k] = sz;
     }
     const unsigned cell = (unsigned)((z * p.ny + y) * p.nx + x);
+    unsigned row[3][3];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const int a = Lat<D>::ex(i) + 1, b = Lat<D>::ey(i) + 1, c = Lat<D>::ez(i) + 1;
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) row[c][b] = (unsigned)((zs[c] * p.ny + ys[b]) * p.nx);
+    sfor<Lat<D>::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int a = Lat<D>::ex(i) + 1, b = Lat<D>::ey(i) + 1, c = Lat<D>::ez(i) + 1;
+        constexpr R w = (R)weight<D>(i);
         R d;
         if (WALLS && (xo[a] || yo[b] || zo[c])) {
             d = Codec<S>::ld(src + (Lat<D>::opp(i) * N + cell));
             R wx = 0, wy = 0, wz = 0, cnt = 0;
             // slot 2 (e = +1) crosses the lower wall (side 0), slot 0 (e = -1) the upper (side 1)
-            if (xo[a]) { const int s = (a == 2) ? 0 : 1; wx += (R)p.uw[0][s][0]; wy += (R)p.uw[0][s][1]; wz += (R)p.uw[0][s][2]; cnt += 1; }
-            if (yo[b]) { const int s = (b == 2) ? 0 : 1; wx += (R)p.uw[1][s][0]; wy += (R)p.uw[1][s][1]; wz += (R)p.uw[1][s][2]; cnt += 1; }
-            if (zo[c]) { const int s = (c == 2) ? 0 : 1; wx += (R)p.uw[2][s][0]; wy += (R)p.uw[2][s][1]; wz += (R)p.uw[2][s][2]; cnt += 1; }
-            const R eu = (R)Lat<D>::ex(i) * wx + (R)Lat<D>::ey(i) * wy + (R)Lat<D>::ez(i) * wz;
+            if (xo[a]) { constexpr int s = (a == 2) ? 0 : 1; wx += p.uw[0][s][0]; wy += p.uw[0][s][1]; wz += p.uw[0][s][2]; cnt += 1; }
+            if (yo[b]) { constexpr int s = (b == 2) ? 0 : 1; wx += p.uw[1][s][0]; wy += p.uw[1][s][1]; wz += p.uw[1][s][2]; cnt += 1; }
+            if (zo[c]) { constexpr int s = (c == 2) ? 0 : 1; wx += p.uw[2][s][0]; wy += p.uw[2][s][1]; wz += p.uw[2][s][2]; cnt += 1; }
+            const R eu = R(Lat<D>::ex(i)) * wx + R(Lat<D>::ey(i)) * wy + R(Lat<D>::ez(i)) * wz;
             d += R(6) * eu / cnt;
         } else {
-            const unsigned sc = (unsigned)((zs[c] * p.ny + ys[b]) * p.nx + xs[a]);
-            d = Codec<S>::ld(src + (i * N + sc));
+            d = Codec<S>::ld(src + (i * N + row[c][b] + (unsigned)xs[a]));
         }
-        h[slot<D>(i)] = d * (R)weight<D>(i);
-    }
+        h[slot<D>(i)] = d * w;
+    });
 }
 
 // ------------------------------------------------------------------------------------------
@@ -223,28 +271,28 @@ template <int D, class R> struct Hydro {
 };
 
 template <int D, class R, bool GEN = true>
-__device__ __forceinline__ Hydro<D, R> hydro(const R (&h)[Lat<D>::Q], const R F[3], const Params& p) {
+__device__ __forceinline__ Hydro<D, R> hydro(const R (&h)[Lat<D>::Q], const R F[3], const PR<R>& p) {
     constexpr int NL = Lat<D>::Q / 3;
     Hydro<D, R> o;
+    R s0[NL];
     R drho = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
-        const R s0 = h[3 * l] + h[3 * l + 1] + h[3 * l + 2];
-        drho += s0;
+        s0[l] = h[3 * l] + h[3 * l + 1] + h[3 * l + 2];
+        drho += s0[l];
         jx += h[3 * l + 2] - h[3 * l];
-        const int b = l % 3, c = l / 3;
-        if (b == 2) jy += s0;
-        if (b == 0) jy -= s0;
-        if constexpr (D == 3) {
-            if (c == 2) jz += s0;
-            if (c == 0) jz -= s0;
-        }
+    }
+#pragma unroll
+    for (int c = 0; c < NL / 3; ++c) jy += s0[3 * c + 2] - s0[3 * c];
+    if constexpr (D == 3) {
+#pragma unroll
+        for (int b = 0; b < 3; ++b) jz += s0[6 + b] - s0[b];
     }
     o.drho = drho;
-    o.jx = jx + R(0.5) * F[0];
-    o.jy = jy + R(0.5) * F[1];
-    o.jz = jz + R(0.5) * F[2];
-    const R inv = R(1) / ((GEN && p.reduced) ? (R)p.rho0 : R(1) + drho);
+    o.jx = fma(R(0.5), F[0], jx);
+    o.jy = fma(R(0.5), F[1], jy);
+    o.jz = fma(R(0.5), F[2], jz);
+    const R inv = rcp((GEN && p.reduced) ? p.rho0 : R(1) + drho);
     o.ux = o.jx * inv;
     o.uy = o.jy * inv;
     o.uz = (D == 3) ? o.jz * inv : R(0);
@@ -255,15 +303,16 @@ __device__ __forceinline__ Hydro<D, R> hydro(const R (&h)[Lat<D>::Q], const R F[
 template <int D, class R>
 __device__ __forceinline__ void central_forward(R (&m)[Lat<D>::Q], R ux, R uy, R uz) {
     constexpr int NL = Lat<D>::Q / 3;
+    const R tx = ux + ux, ty = uy + uy, tz = uz + uz, qx = ux * ux, qy = uy * uy, qz = uz * uz;
 #pragma unroll
-    for (int l = 0; l < NL; ++l) fwd1(m[3 * l], m[3 * l + 1], m[3 * l + 2], ux);
+    for (int l = 0; l < NL; ++l) fwd1(m[3 * l], m[3 * l + 1], m[3 * l + 2], ux, tx, qx);
 #pragma unroll
     for (int c = 0; c < Lat<D>::NZ; ++c)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) fwd1(m[9 * c + a], m[9 * c + 3 + a], m[9 * c + 6 + a], uy);
+        for (int a = 0; a < 3; ++a) fwd1(m[9 * c + a], m[9 * c + 3 + a], m[9 * c + 6 + a], uy, ty, qy);
     if constexpr (D == 3) {
 #pragma unroll
-        for (int t = 0; t < 9; ++t) fwd1(m[t], m[9 + t], m[18 + t], uz);
+        for (int t = 0; t < 9; ++t) fwd1(m[t], m[9 + t], m[18 + t], uz, tz, qz);
     }
 }
 
@@ -271,24 +320,25 @@ __device__ __forceinline__ void central_forward(R (&m)[Lat<D>::Q], R ux, R uy, R
 template <int D, class R>
 __device__ __forceinline__ void central_inverse(R (&m)[Lat<D>::Q], R ux, R uy, R uz) {
     constexpr int NL = Lat<D>::Q / 3;
+    const R tx = ux + ux, ty = uy + uy, tz = uz + uz, qx = ux * ux, qy = uy * uy, qz = uz * uz;
     if constexpr (D == 3) {
 #pragma unroll
-        for (int t = 0; t < 9; ++t) inv1(m[t], m[9 + t], m[18 + t], uz);
+        for (int t = 0; t < 9; ++t) inv1(m[t], m[9 + t], m[18 + t], uz, tz, qz);
     }
 #pragma unroll
     for (int c = 0; c < Lat<D>::NZ; ++c)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) inv1(m[9 * c + a], m[9 * c + 3 + a], m[9 * c + 6 + a], uy);
+        for (int a = 0; a < 3; ++a) inv1(m[9 * c + a], m[9 * c + 3 + a], m[9 * c + 6 + a], uy, ty, qy);
 #pragma unroll
-    for (int l = 0; l < NL; ++l) inv1(m[3 * l], m[3 * l + 1], m[3 * l + 2], ux);
+    for (int l = 0; l < NL; ++l) inv1(m[3 * l], m[3 * l + 1], m[3 * l + 2], ux, tx, qx);
 }
 
 // prod_{d in S}(1/3 + q_d) - 3^{-|S|} without cancellation (all terms are non-negative)
-template <class R> __device__ __forceinline__ R excess(const R* q, bool x, bool y, bool z) {
+template <class R, bool X, bool Y, bool Z> __device__ __forceinline__ R excess(const R* q) {
     R A = 0, tk = 1;
-    if (x) { A = (R(1) / 3 + q[0]) * A + q[0] * tk; tk *= R(1) / 3; }
-    if (y) { A = (R(1) / 3 + q[1]) * A + q[1] * tk; tk *= R(1) / 3; }
-    if (z) { A = (R(1) / 3 + q[2]) * A + q[2] * tk; tk *= R(1) / 3; }
+    if constexpr (X) { A = (R(1) / 3 + q[0]) * A + q[0] * tk; tk *= R(1) / 3; }
+    if constexpr (Y) { A = (R(1) / 3 + q[1]) * A + q[1] * tk; tk *= R(1) / 3; }
+    if constexpr (Z) { A = (R(1) / 3 + q[2]) * A + q[2] * tk; tk *= R(1) / 3; }
     return A;
 }
 
@@ -298,7 +348,7 @@ template <class R> __device__ __forceinline__ R excess(const R* q, bool x, bool 
 // Out: h holds the post-collision deviation populations.
 // ------------------------------------------------------------------------------------------
 template <int D, class R, class FT>
-__device__ __forceinline__ void collide(R (&m)[Lat<D>::Q], const R F[3], const Params& p, R cs_eff) {
+__device__ __forceinline__ void collide(R (&m)[Lat<D>::Q], const R F[3], const PR<R>& p, R cs_eff) {
     constexpr int Q = Lat<D>::Q;
     const Hydro<D, R> hy = hydro<D, R, FT::GEN>(m, F, p);
     const R drho = hy.drho, rho = R(1) + hy.drho;
@@ -309,36 +359,41 @@ __device__ __forceinline__ void collide(R (&m)[Lat<D>::Q], const R F[3], const P
     const R cw[3][3] = {{R(1), -u[0], R(1) / 3 + q[0]},
                         {R(1), -u[1], R(1) / 3 + q[1]},
                         {R(1), -u[2], R(1) / 3 + q[2]}};
-    const R irho = R(1) / rho;
+    const R irho = rcp(rho);
     const R Fr[3] = {F[0] * irho, F[1] * irho, F[2] * irho};
-    const R third = R(1) / 3;
+    constexpr R third = R(1) / 3;
 
     // second order: non-equilibrium stress Pi = kappa - c_s^2 rho delta (kappa = kbar at order 2)
-    const R Pxx = m[midx(2, 0, 0)] + q[0] - drho * third;
-    const R Pyy = m[midx(0, 2, 0)] + q[1] - drho * third;
-    const R Pxy = m[midx(1, 1, 0)] + u[0] * u[1];
+    const R Pxx = m[midx(2, 0, 0)] + fma(-drho, third, q[0]);
+    const R Pyy = m[midx(0, 2, 0)] + fma(-drho, third, q[1]);
+    const R Pxy = fma(u[0], u[1], m[midx(1, 1, 0)]);
     R Pzz = R(0), Pxz = R(0), Pyz = R(0);
     if constexpr (D == 3) {
-        Pzz = m[midx(0, 0, 2)] + q[2] - drho * third;
-        Pxz = m[midx(1, 0, 1)] + u[0] * u[2];
-        Pyz = m[midx(0, 1, 1)] + u[1] * u[2];
+        Pzz = m[midx(0, 0, 2)] + fma(-drho, third, q[2]);
+        Pxz = fma(u[0], u[2], m[midx(1, 0, 1)]);
+        Pyz = fma(u[1], u[2], m[midx(0, 1, 1)]);
     }
 
-    R tau = (R)p.tau0;
-    if (FT::LES && cs_eff > R(0)) {
-        const R Qn = sqrt(Pxx * Pxx + Pyy * Pyy + Pzz * Pzz + R(2) * (Pxy * Pxy + Pxz * Pxz + Pyz * Pyz));
-        tau = R(0.5) * (tau + sqrt(tau * tau + R(25.455844122715710878) * cs_eff * cs_eff * Qn * irho));
+    R wnu;
+    if constexpr (FT::LES) {
+        R tau = p.tau0;
+        if (cs_eff > R(0)) {
+            const R Qn = sqrt(Pxx * Pxx + Pyy * Pyy + Pzz * Pzz + R(2) * (Pxy * Pxy + Pxz * Pxz + Pyz * Pyz));
+            tau = R(0.5) * (tau + sqrt(tau * tau + R(25.455844122715710878) * cs_eff * cs_eff * Qn * irho));
+        }
+        wnu = rcp(tau);
+    } else {
+        wnu = rcp(p.tau0);
     }
-    const R wnu = R(1) / tau;
-    const R wb = (p.omega_bulk > 0.0) ? (R)p.omega_bulk : wnu;
+    const R wb = (p.omega_bulk > R(0)) ? p.omega_bulk : wnu;
 
     // kappa of f at second order, used by the source recursion (sigma = 0 at second order)
     R kap[Q];
-    kap[midx(2, 0, 0)] = Pxx + rho * third;
-    kap[midx(0, 2, 0)] = Pyy + rho * third;
+    kap[midx(2, 0, 0)] = fma(rho, third, Pxx);
+    kap[midx(0, 2, 0)] = fma(rho, third, Pyy);
     kap[midx(1, 1, 0)] = Pxy;
     if constexpr (D == 3) {
-        kap[midx(0, 0, 2)] = Pzz + rho * third;
+        kap[midx(0, 0, 2)] = fma(rho, third, Pzz);
         kap[midx(1, 0, 1)] = Pxz;
         kap[midx(0, 1, 1)] = Pyz;
     }
@@ -346,72 +401,72 @@ __device__ __forceinline__ void collide(R (&m)[Lat<D>::Q], const R F[3], const P
     // relaxed second order: trace with omega_b, deviator and off-diagonal with omega_nu
     const R tr = Pxx + Pyy + Pzz;
     const R corr = (wnu - wb) * tr * (R(1) / D);
-    const R Txx = (R(1) - wnu) * Pxx + corr;
-    const R Tyy = (R(1) - wnu) * Pyy + corr;
-    const R Tzz = (R(1) - wnu) * Pzz + corr;
-    const R Txy = (R(1) - wnu) * Pxy;
-    const R Txz = (R(1) - wnu) * Pxz;
-    const R Tyz = (R(1) - wnu) * Pyz;
-    const R Tdiag[3] = {Txx, Tyy, Tzz};
-    const R w3 = (R)p.omega3, w4 = (R)p.omega4;
+    const R omn = R(1) - wnu;
+    const R Txx = fma(omn, Pxx, corr);
+    const R Tyy = fma(omn, Pyy, corr);
+    const R Tzz = fma(omn, Pzz, corr);
+    const R Txy = omn * Pxy;
+    const R Txz = omn * Pxz;
+    const R Tyz = omn * Pyz;
+    const R w3 = p.omega3, w4 = p.omega4;
+    const bool factorized = FT::GEN && p.attractor != 0;
 
-    // orders >= 3: source by the hierarchical identity, attractor, relaxation
-#pragma unroll
-    for (int n = 3; n <= 2 * D; ++n) {
-#pragma unroll
-        for (int t = 0; t < Q; ++t) {
-            if (ord(t) != n) continue;
-            const int a = ex_a(t), b = ex_b(t), c = ex_c(t);
-            R s = 0;
-            if (a > 0) s += R(a) * Fr[0] * kap[t > 0 ? t - 1 : 0];
-            if (b > 0) s += R(b) * Fr[1] * kap[t > 2 ? t - 3 : 0];
-            if (c > 0) s += R(c) * Fr[2] * kap[t > 8 ? t - 9 : 0];
-            const R kw = cw[0][a] * cw[1][b] * cw[2][c];
-            if (n < 2 * D) kap[t] = m[t] + kw + R(0.5) * s;
-            const bool even = (a % 2 == 0) && (b % 2 == 0) && (c % 2 == 0);
-            const int twos = (a == 2) + (b == 2) + (c == 2);
-            R DM;
-            if (!FT::GEN || p.attractor == 0) {
-                DM = even ? drho * (R)third_pow(twos) - excess(q, a == 2, b == 2, c == 2) : -kw;
-            } else {
-                // factorized attractor (Sec. 11): products of relaxed second-order moments / rho^(k-1)
-                const int ones = (a == 1) + (b == 1) + (c == 1);
-                if (ones == 0) {
-                    const R pt[3] = {Txx * irho, Tyy * irho, Tzz * irho};
-                    const R Ap = excess(pt, a == 2, b == 2, c == 2);
-                    const R Aq = excess(q, a == 2, b == 2, c == 2);
-                    R prodp = 1;
-                    if (a == 2) prodp *= third + pt[0];
-                    if (b == 2) prodp *= third + pt[1];
-                    if (c == 2) prodp *= third + pt[2];
-                    DM = drho * prodp + (Ap - Aq);
-                } else if (ones == 2 && twos == 1) {
-                    const int dtwo = (a == 2) ? 0 : (b == 2) ? 1 : 2;
-                    const R Toff = (a != 1) ? Tyz : (b != 1) ? Txz : Txy;
-                    const R uoff = (a != 1) ? u[1] * u[2] : (b != 1) ? u[0] * u[2] : u[0] * u[1];
-                    DM = Toff * (third + Tdiag[dtwo] * irho) - (third + q[dtwo]) * uoff;
-                } else {
-                    DM = -kw;
+    // orders >= 3 in increasing order: source by the hierarchical identity, attractor, relaxation
+    sfor<2 * D + 1>([&](auto NI) {
+        constexpr int n = decltype(NI)::value;
+        sfor<Q>([&](auto TI) {
+            constexpr int t = decltype(TI)::value;
+            if constexpr (n >= 3 && ord(t) == n) {
+                constexpr int a = ex_a(t), b = ex_b(t), c = ex_c(t);
+                R s = R(0);
+                if constexpr (a > 0) s = fma(R(a) * Fr[0], kap[t - 1], s);
+                if constexpr (b > 0) s = fma(R(b) * Fr[1], kap[t - 3], s);
+                if constexpr (c > 0) s = fma(R(c) * Fr[2], kap[t - 9], s);
+                const R kw = cw[0][a] * cw[1][b] * cw[2][c];
+                if constexpr (ord(t) < 2 * D) kap[t] = m[t] + kw + R(0.5) * s;
+                constexpr bool even = (a % 2 == 0) && (b % 2 == 0) && (c % 2 == 0);
+                constexpr int twos = (a == 2) + (b == 2) + (c == 2);
+                constexpr R tp = (R)third_pow(twos);
+                R DM;
+                if constexpr (even) DM = fma(drho, tp, -excess<R, a == 2, b == 2, c == 2>(q));
+                else DM = -kw;
+                if (factorized) {
+                    // Sec. 11: products of relaxed second-order moments / rho^(k-1)
+                    constexpr int ones = (a == 1) + (b == 1) + (c == 1);
+                    if constexpr (ones == 0) {
+                        const R pt[3] = {Txx * irho, Tyy * irho, Tzz * irho};
+                        R prodp = 1;
+                        if constexpr (a == 2) prodp *= third + pt[0];
+                        if constexpr (b == 2) prodp *= third + pt[1];
+                        if constexpr (c == 2) prodp *= third + pt[2];
+                        DM = drho * prodp + (excess<R, a == 2, b == 2, c == 2>(pt) - excess<R, a == 2, b == 2, c == 2>(q));
+                    } else if constexpr (ones == 2 && twos == 1) {
+                        constexpr int dtwo = (a == 2) ? 0 : (b == 2) ? 1 : 2;
+                        const R Tdg = dtwo == 0 ? Txx : dtwo == 1 ? Tyy : Tzz;
+                        const R Toff = (a != 1) ? Tyz : (b != 1) ? Txz : Txy;
+                        const R uoff = (a != 1) ? u[1] * u[2] : (b != 1) ? u[0] * u[2] : u[0] * u[1];
+                        DM = Toff * (third + Tdg * irho) - (third + q[dtwo]) * uoff;
+                    }
                 }
+                const R w = (ord(t) == 3) ? w3 : w4;
+                m[t] = fma(R(1) - w, m[t] + R(0.5) * s, fma(w, DM, R(0.5) * s));
             }
-            const R w = (n == 3) ? w3 : w4;
-            m[t] = (R(1) - w) * (m[t] + R(0.5) * s) + w * DM + R(0.5) * s;
-        }
-    }
+        });
+    });
 
     // second order back to deviations of the weights' moments
-    m[midx(2, 0, 0)] = Txx + drho * third - q[0];
-    m[midx(0, 2, 0)] = Tyy + drho * third - q[1];
-    m[midx(1, 1, 0)] = Txy - u[0] * u[1];
+    m[midx(2, 0, 0)] = Txx + fma(drho, third, -q[0]);
+    m[midx(0, 2, 0)] = Tyy + fma(drho, third, -q[1]);
+    m[midx(1, 1, 0)] = fma(-u[0], u[1], Txy);
     if constexpr (D == 3) {
-        m[midx(0, 0, 2)] = Tzz + drho * third - q[2];
-        m[midx(1, 0, 1)] = Txz - u[0] * u[2];
-        m[midx(0, 1, 1)] = Tyz - u[1] * u[2];
+        m[midx(0, 0, 2)] = Tzz + fma(drho, third, -q[2]);
+        m[midx(1, 0, 1)] = fma(-u[0], u[2], Txz);
+        m[midx(0, 1, 1)] = fma(-u[1], u[2], Tyz);
     }
     // first order: collision invariant plus the source sigma_x = F_x
-    m[midx(1, 0, 0)] = hy.jx + R(0.5) * F[0] - drho * u[0];
-    m[midx(0, 1, 0)] = hy.jy + R(0.5) * F[1] - drho * u[1];
-    if constexpr (D == 3) m[midx(0, 0, 1)] = hy.jz + R(0.5) * F[2] - drho * u[2];
+    m[midx(1, 0, 0)] = fma(-drho, u[0], fma(R(0.5), F[0], hy.jx));
+    m[midx(0, 1, 0)] = fma(-drho, u[1], fma(R(0.5), F[1], hy.jy));
+    if constexpr (D == 3) m[midx(0, 0, 1)] = fma(-drho, u[2], fma(R(0.5), F[2], hy.jz));
     // zeroth order unchanged (m[0] = drho)
 
     central_inverse<D, R>(m, u[0], u[1], u[2]);
@@ -427,24 +482,24 @@ __device__ __forceinline__ void equilibrium(R (&m)[Lat<D>::Q], R rho, R ux, R uy
                         {R(1), -u[1], R(1) / 3 + q[1]},
                         {R(1), -u[2], R(1) / 3 + q[2]}};
     const R drho = rho - R(1);
-    const R irho = R(1) / rho;
-#pragma unroll
-    for (int t = 0; t < Q; ++t) {
-        const int a = ex_a(t), b = ex_b(t), c = ex_c(t);
-        const int n = ord(t);
-        const bool even = (a % 2 == 0) && (b % 2 == 0) && (c % 2 == 0);
-        const int twos = (a == 2) + (b == 2) + (c == 2);
+    sfor<Q>([&](auto TI) {
+        constexpr int t = decltype(TI)::value;
+        constexpr int a = ex_a(t), b = ex_b(t), c = ex_c(t);
+        constexpr bool even = (a % 2 == 0) && (b % 2 == 0) && (c % 2 == 0);
+        constexpr int twos = (a == 2) + (b == 2) + (c == 2);
+        constexpr R tp = (R)third_pow(twos);
         // sigma^M by the identity on the Maxwellian moments: non-zero only for one odd axis
         R s = 0;
-        if (a == 1 && (b % 2 == 0) && (c % 2 == 0)) s += F[0] * irho * rho * (R)third_pow(twos);
-        if (b == 1 && (a % 2 == 0) && (c % 2 == 0)) s += F[1] * irho * rho * (R)third_pow(twos);
-        if (c == 1 && (a % 2 == 0) && (b % 2 == 0)) s += F[2] * irho * rho * (R)third_pow(twos);
+        if constexpr (a == 1 && (b % 2 == 0) && (c % 2 == 0)) s += F[0] * tp;
+        if constexpr (b == 1 && (a % 2 == 0) && (c % 2 == 0)) s += F[1] * tp;
+        if constexpr (c == 1 && (a % 2 == 0) && (b % 2 == 0)) s += F[2] * tp;
         const R kw = cw[0][a] * cw[1][b] * cw[2][c];
         R DM;
-        if (n == 0) DM = drho;
-        else DM = even ? drho * (R)third_pow(twos) - excess(q, a == 2, b == 2, c == 2) : -kw;
+        if constexpr (ord(t) == 0) DM = drho;
+        else if constexpr (even) DM = drho * tp - excess<R, a == 2, b == 2, c == 2>(q);
+        else DM = -kw;
         m[t] = DM - R(0.5) * s;
-    }
+    });
     central_inverse<D, R>(m, u[0], u[1], u[2]);
 }
 

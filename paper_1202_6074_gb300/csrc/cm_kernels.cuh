@@ -21,26 +21,26 @@ inline dim3 cell_grid(const Params& p, dim3 b) {
 }
 
 template <class R, bool FIELD = true>
-__device__ __forceinline__ void load_force(const R* __restrict__ Ff, const Params& p, unsigned cell, R F[3]) {
+__device__ __forceinline__ void load_force(const R* __restrict__ Ff, const PR<R>& p, unsigned cell, R F[3]) {
     if (FIELD && p.has_field) {
-        const unsigned N = (unsigned)p.N;
+        const unsigned N = p.N;
         F[0] = __ldg(Ff + cell);
         F[1] = __ldg(Ff + (N + cell));
         F[2] = __ldg(Ff + (2 * N + cell));
     } else {
-        F[0] = (R)p.F[0];
-        F[1] = (R)p.F[1];
-        F[2] = (R)p.F[2];
+        F[0] = p.F[0];
+        F[1] = p.F[1];
+        F[2] = p.F[2];
     }
 }
 
 template <class R, bool LES = true>
-__device__ __forceinline__ R smagorinsky_constant(const Params& p, int y) {
+__device__ __forceinline__ R smagorinsky_constant(const PR<R>& p, int y) {
     if (!LES || !p.les) return R(0);
-    R c = (R)p.cs;
+    R c = p.cs;
     if (p.vd) {
         const R yw = fmin((R)y + R(0.5), (R)p.ny - R(0.5) - (R)y);
-        c *= R(1) - exp(-yw * (R)p.vd_utau_nu / (R)p.vd_aplus);
+        c *= R(1) - exp(-yw * p.vd_utau_nu / p.vd_aplus);
     }
     return c;
 }
@@ -48,7 +48,7 @@ __device__ __forceinline__ R smagorinsky_constant(const Params& p, int y) {
 // ---- fused pull + collide + store --------------------------------------------------------
 template <int D, class S, class FT>
 __global__ void __launch_bounds__(kBlock, CM_STEP_MIN_BLOCKS) k_step(const S* __restrict__ src, S* __restrict__ dst,
-                                                const typename Codec<S>::R* __restrict__ Ff, Params p) {
+                                                const typename Codec<S>::R* __restrict__ Ff, PR<typename Codec<S>::R> p) {
     using R = typename Codec<S>::R;
     constexpr int Q = Lat<D>::Q;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -56,20 +56,23 @@ __global__ void __launch_bounds__(kBlock, CM_STEP_MIN_BLOCKS) k_step(const S* __
     const int z = blockIdx.z;
     if (x >= p.nx || y >= p.ny) return;
     const unsigned cell = (unsigned)((z * p.ny + y) * p.nx + x);
-    const unsigned N = (unsigned)p.N;
+    const unsigned N = p.N;
     R h[Q];
     gather<D, S, FT::WALLS>(src, x, y, z, p, h);
     R F[3];
     load_force<R, FT::FIELD>(Ff, p, cell, F);
     collide<D, R, FT>(h, F, p, smagorinsky_constant<R, FT::LES>(p, y));
-#pragma unroll
-    for (int i = 0; i < Q; ++i) Codec<S>::st(dst + (i * N + cell), h[slot<D>(i)] * (R)inv_weight<D>(i));
+    sfor<Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr R iw = (R)inv_weight<D>(i);
+        Codec<S>::st(dst + (i * N + cell), h[slot<D>(i)] * iw);
+    });
 }
 
 // ---- density and velocity of the pulled field ----------------------------------------------
 template <int D, class S, bool WALLS>
 __global__ void __launch_bounds__(kBlock) k_moments(const S* __restrict__ src, const typename Codec<S>::R* __restrict__ Ff,
-                                                   Params p, double* __restrict__ rho, double* __restrict__ u) {
+                                                   PR<typename Codec<S>::R> p, double* __restrict__ rho, double* __restrict__ u) {
     using R = typename Codec<S>::R;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -92,7 +95,7 @@ __global__ void __launch_bounds__(kBlock) k_moments(const S* __restrict__ src, c
 // ---- initial state: equilibrium at the cell, then the inverse of the pull -----------------
 template <int D, class S>
 __global__ void __launch_bounds__(kBlock) k_equilibrium(S* __restrict__ dst, const typename Codec<S>::R* __restrict__ Ff,
-                                                       Params p, const double* __restrict__ rho, const double* __restrict__ u) {
+                                                       PR<typename Codec<S>::R> p, const double* __restrict__ rho, const double* __restrict__ u) {
     using R = typename Codec<S>::R;
     constexpr int Q = Lat<D>::Q;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -105,20 +108,22 @@ __global__ void __launch_bounds__(kBlock) k_equilibrium(S* __restrict__ dst, con
     const double r = rho ? rho[cell] : 1.0;
     double ux = u ? u[cell] : 0.0, uy = u ? u[p.N + cell] : 0.0, uz = (u && D == 3) ? u[2 * p.N + cell] : 0.0;
     if (p.reduced) {   // momentum rho0 u: centre the equilibrium on rho0 u / rho
-        ux *= p.rho0 / r;
-        uy *= p.rho0 / r;
-        uz *= p.rho0 / r;
+        ux *= (double)p.rho0 / r;
+        uy *= (double)p.rho0 / r;
+        uz *= (double)p.rho0 / r;
     }
     R m[Q];
     equilibrium<D, R>(m, (R)r, (R)ux, (R)uy, (R)uz, F);
-#pragma unroll
-    for (int i = 0; i < Q; ++i)
-        Codec<S>::st(dst + (long long)i * p.N + cell, m[slot<D>(i)] * (R)inv_weight<D>(i));
+    sfor<Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr R iw = (R)inv_weight<D>(i);
+        Codec<S>::st(dst + ((unsigned)i * p.N + cell), m[slot<D>(i)] * iw);
+    });
 }
 
 // s_i(x) = fbar_i(x + e_i), or the reflected value when x + e_i is behind a wall
 template <int D, class S>
-__global__ void __launch_bounds__(kBlock) k_unstream(const S* __restrict__ fb, S* __restrict__ dst, Params p) {
+__global__ void __launch_bounds__(kBlock) k_unstream(const S* __restrict__ fb, S* __restrict__ dst, PR<typename Codec<S>::R> p) {
     using R = typename Codec<S>::R;
     constexpr int Q = Lat<D>::Q;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -144,9 +149,9 @@ __global__ void __launch_bounds__(kBlock) k_unstream(const S* __restrict__ fb, S
                     const int side = (t[a] < 0) ? 0 : 1;
                     out = true;
                     cnt += 1;
-                    wsum[0] += (R)p.uw[a][side][0];
-                    wsum[1] += (R)p.uw[a][side][1];
-                    wsum[2] += (R)p.uw[a][side][2];
+                    wsum[0] += p.uw[a][side][0];
+                    wsum[1] += p.uw[a][side][1];
+                    wsum[2] += p.uw[a][side][2];
                     t[a] = xyz[a];
                 }
             }
@@ -177,7 +182,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 template <int D, class S, bool WALLS>
 __global__ void __launch_bounds__(kRedThreads) k_reduce_partial(const S* __restrict__ src,
                                                                const typename Codec<S>::R* __restrict__ Ff,
-                                                               Params p, double* __restrict__ part) {
+                                                               PR<typename Codec<S>::R> p, double* __restrict__ part) {
     using R = typename Codec<S>::R;
     double acc[5] = {0, 0, 0, 0, 0};
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -260,7 +265,7 @@ template <int D, class S, class FT>
 void launch_step_ft(const void* src, void* dst, const void* Ff, const Params& p, cudaStream_t st) {
     using R = typename Codec<S>::R;
     const dim3 b = cell_block(p.nx), g = cell_grid(p, b);
-    k_step<D, S, FT><<<g, b, 0, st>>>((const S*)src, (S*)dst, (const R*)Ff, p);
+    k_step<D, S, FT><<<g, b, 0, st>>>((const S*)src, (S*)dst, (const R*)Ff, typed<R>(p));
 }
 
 template <int D, class S, bool W, bool L, bool F>
@@ -291,9 +296,9 @@ cudaError_t launch_moments(const void* src, const void* Ff, const Params& p, dou
     using R = typename Codec<S>::R;
     const dim3 b = cell_block(p.nx), g = cell_grid(p, b);
     if (has_walls(p))
-        k_moments<D, S, true><<<g, b, 0, st>>>((const S*)src, (const R*)Ff, p, rho, u);
+        k_moments<D, S, true><<<g, b, 0, st>>>((const S*)src, (const R*)Ff, typed<R>(p), rho, u);
     else
-        k_moments<D, S, false><<<g, b, 0, st>>>((const S*)src, (const R*)Ff, p, rho, u);
+        k_moments<D, S, false><<<g, b, 0, st>>>((const S*)src, (const R*)Ff, typed<R>(p), rho, u);
     return cudaGetLastError();
 }
 
@@ -302,8 +307,8 @@ cudaError_t launch_init(void* tmp, void* dst, const void* Ff, const Params& p, c
                         cudaStream_t st) {
     using R = typename Codec<S>::R;
     const dim3 b = cell_block(p.nx), g = cell_grid(p, b);
-    k_equilibrium<D, S><<<g, b, 0, st>>>((S*)tmp, (const R*)Ff, p, rho, u);
-    k_unstream<D, S><<<g, b, 0, st>>>((const S*)tmp, (S*)dst, p);
+    k_equilibrium<D, S><<<g, b, 0, st>>>((S*)tmp, (const R*)Ff, typed<R>(p), rho, u);
+    k_unstream<D, S><<<g, b, 0, st>>>((const S*)tmp, (S*)dst, typed<R>(p));
     return cudaGetLastError();
 }
 
@@ -317,9 +322,9 @@ cudaError_t launch_reduce(const void* src, const void* Ff, const Params& p, doub
     using R = typename Codec<S>::R;
     const int nb = reduce_blocks(p);
     if (has_walls(p))
-        k_reduce_partial<D, S, true><<<nb, kRedThreads, 0, st>>>((const S*)src, (const R*)Ff, p, part);
+        k_reduce_partial<D, S, true><<<nb, kRedThreads, 0, st>>>((const S*)src, (const R*)Ff, typed<R>(p), part);
     else
-        k_reduce_partial<D, S, false><<<nb, kRedThreads, 0, st>>>((const S*)src, (const R*)Ff, p, part);
+        k_reduce_partial<D, S, false><<<nb, kRedThreads, 0, st>>>((const S*)src, (const R*)Ff, typed<R>(p), part);
     k_reduce_final<<<1, kRedThreads, 0, st>>>(part, nb, out);
     return cudaGetLastError();
 }

@@ -300,10 +300,22 @@ def test_invalid_arguments_return_errors(cm):
     with pytest.raises(cm.CmlbmError) as e:
         s.step(-1)
     assert e.value.code == cm.ERR_INVALID
-    bad = s.new_state()
-    with pytest.raises(cm.CmlbmError):
-        s.step_buffers(bad, bad)
+    st = s.new_state()
     with pytest.raises(cm.CmlbmError) as e:
-        s.adjoint_terminal(bad, torch.zeros(3, 64, dtype=torch.float64, device="cuda"), bad,
-                           torch.zeros(3, 64, dtype=torch.float64, device="cuda"))
+        s.step_buffers(st, st)
+    assert e.value.code == cm.ERR_INVALID
+    lam = torch.zeros((27, 4, 4, 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(cm.CmlbmError) as e:
+        s.step_adjoint(st, lam, lam, torch.zeros(3, 64, dtype=torch.float64, device="cuda"))
+    assert e.value.code == cm.ERR_INVALID
+    with pytest.raises(cm.CmlbmError) as e:
+        s.set_state(torch.zeros(5, dtype=torch.float32, device="cuda"))
+    assert e.value.code == cm.ERR_INVALID
     s.close()
+    # the adjoint is not provided for 16-bit storage or with the eddy viscosity
+    for kw in (dict(storage="bf16"), dict(storage="f32", smagorinsky_cs=0.1)):
+        b = cm.Solver(lattice="D3Q27", nx=4, ny=4, nz=4, **kw)
+        with pytest.raises(cm.CmlbmError) as e:
+            b.step_adjoint(b.new_state(), lam, torch.zeros_like(lam), torch.zeros(3, 64, dtype=torch.float64, device="cuda"))
+        assert e.value.code == cm.ERR_UNSUPPORTED
+        b.close()
