@@ -251,12 +251,14 @@ class Solver:
 
     def get_state(self, out=None):
         out = self.new_state() if out is None else out
-        self._check(self.lib.cmlbm_get_state(self.h, _ptr(out), self.state_bytes, DEVICE))
+        nbytes = out.numel() * out.element_size()
+        self._check(self.lib.cmlbm_get_state(self.h, _ptr(out), nbytes, DEVICE))
         return out
 
     def set_state(self, s):
         s = s.to(self.device, self.state_dtype).contiguous()
-        self._check(self.lib.cmlbm_set_state(self.h, _ptr(s), self.state_bytes, DEVICE))
+        nbytes = s.numel() * s.element_size()
+        self._check(self.lib.cmlbm_set_state(self.h, _ptr(s), nbytes, DEVICE))
         torch.cuda.current_stream(self.device).synchronize()
 
     # ---- adjoint ----------------------------------------------------------------------

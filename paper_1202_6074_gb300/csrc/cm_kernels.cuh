@@ -7,10 +7,13 @@ namespace cm {
 
 // Threads per block of the cell kernels and the block shape for a given nx.
 constexpr int kBlock = 128;
-// Minimum resident blocks per SM requested from the register allocator for the step kernel.
+// Minimum resident blocks per SM requested from the register allocator for the FP32-arithmetic
+// step kernel: 8 blocks of 128 threads caps it at 64 registers (measured fastest on GB300 for
+// both FP32 and 16-bit storage); FP64 arithmetic is left unconstrained.
 #ifndef CM_STEP_MIN_BLOCKS
-#define CM_STEP_MIN_BLOCKS 1
+#define CM_STEP_MIN_BLOCKS 8
 #endif
+template <class S> constexpr int step_min_blocks() { return sizeof(typename Codec<S>::R) == 8 ? 1 : CM_STEP_MIN_BLOCKS; }
 inline dim3 cell_block(int nx) {
     int bx = 32;
     while (bx < kBlock && bx < nx) bx *= 2;
@@ -47,7 +50,7 @@ __device__ __forceinline__ R smagorinsky_constant(const PR<R>& p, int y) {
 
 // ---- fused pull + collide + store --------------------------------------------------------
 template <int D, class S, class FT>
-__global__ void __launch_bounds__(kBlock, CM_STEP_MIN_BLOCKS) k_step(const S* __restrict__ src, S* __restrict__ dst,
+__global__ void __launch_bounds__(kBlock, step_min_blocks<S>()) k_step(const S* __restrict__ src, S* __restrict__ dst,
                                                 const typename Codec<S>::R* __restrict__ Ff, PR<typename Codec<S>::R> p) {
     using R = typename Codec<S>::R;
     constexpr int Q = Lat<D>::Q;
