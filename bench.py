@@ -33,6 +33,9 @@ BYTES_PER_CELL = {("D3Q27", "f32"): 216, ("D3Q27", "bf16"): 108, ("D3Q27", "f16"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC = os.path.join(ROOT, "profiles", "traffic.txt")
 FALLBACK_HBM = 6800.0
+# bulk-viscosity rate of the trace of the second-order moments: free in the paper ("adjusted to
+# improve numerical stability"); at tau -> 1/2 a bulk rate equal to the shear rate is unstable
+OMEGA_BULK = 1.0
 
 
 def parse():
@@ -199,11 +202,12 @@ def time_steps(solver, steps, warmup, dist, stream):
 # ------------------------------------------------------------------------------------------
 # forms
 # ------------------------------------------------------------------------------------------
-def run_tgv(cm, n, storage, steps, warmup, dist, clocks=None):
+def run_tgv(cm, n, storage, steps, warmup, dist, clocks=None, kernel="auto"):
     from paper_1202_6074_gb300 import workloads as W
 
     stream = torch.cuda.current_stream()
-    s = cm.Solver(lattice="D3Q27", nx=n, ny=n, nz=n, storage=storage, tau=tgv_tau(n))
+    s = cm.Solver(lattice="D3Q27", nx=n, ny=n, nz=n, storage=storage, tau=tgv_tau(n), omega_bulk=OMEGA_BULK,
+                  kernel=kernel)
     rho, u = W.taylor_green(n, n, n, u0=0.05, xp=torch, device="cuda")
     s.init(rho, u)
     del rho, u
@@ -219,7 +223,8 @@ def run_tgv(cm, n, storage, steps, warmup, dist, clocks=None):
 def run_hit_les(cm, n, storage, steps, warmup, dist):
     from paper_1202_6074_gb300 import workloads as W
 
-    s = cm.Solver(lattice="D3Q27", nx=n, ny=n, nz=n, storage=storage, tau=0.5005, smagorinsky_cs=0.1)
+    s = cm.Solver(lattice="D3Q27", nx=n, ny=n, nz=n, storage=storage, tau=0.5005, smagorinsky_cs=0.1,
+                  omega_bulk=OMEGA_BULK)
     F = W.hit_forcing(n, n, n, seed=1, xp=torch, device="cuda")
     s.set_force((0, 0, 0), F)
     del F
@@ -233,7 +238,7 @@ def run_channel(cm, storage, steps, warmup, dist, nx=1024, ny=256, nz=256):
     u_tau, h = 0.005, ny / 2
     nu0 = u_tau * h / 180.0
     s = cm.Solver(lattice="D3Q27", nx=nx, ny=ny, nz=nz, storage=storage, tau=3 * nu0 + 0.5, smagorinsky_cs=0.1,
-                  van_driest=(26.0, u_tau / nu0), bc=("periodic", "bounceback", "periodic"))
+                  van_driest=(26.0, u_tau / nu0), bc=("periodic", "bounceback", "periodic"), omega_bulk=OMEGA_BULK)
     s.set_force((u_tau * u_tau / h, 0.0, 0.0))
     # laminar-shape start scaled to the bulk speed, with seeded noise (device generator)
     y = (torch.arange(ny, device="cuda", dtype=torch.float64) + 0.5).view(1, ny, 1)
@@ -260,7 +265,7 @@ def e2e(cm, n, storage, steps):
     del rho, u
     rho_o = torch.empty_like(rho_h).pin_memory()
     u_o = torch.empty_like(u_h).pin_memory()
-    s = cm.Solver(lattice="D3Q27", nx=n, ny=n, nz=n, storage=storage, tau=tgv_tau(n))
+    s = cm.Solver(lattice="D3Q27", nx=n, ny=n, nz=n, storage=storage, tau=tgv_tau(n), omega_bulk=OMEGA_BULK)
     lib = s.lib
     P = cm._ptr
     torch.cuda.synchronize()
@@ -284,7 +289,7 @@ def cpu_baseline(n=40, steps=4):
     from paper_1202_6074_gb300 import workloads as W
 
     rho, u = W.taylor_green(n, n, n, u0=0.05)
-    o = OracleSim("D3Q27", n, n, n, Params(tau=tgv_tau(n)))
+    o = OracleSim("D3Q27", n, n, n, Params(tau=tgv_tau(n), omega_bulk=OMEGA_BULK))
     o.init(torch.tensor(rho), torch.tensor(u))
     t0 = time.perf_counter()
     o.step(steps)
@@ -308,7 +313,7 @@ def reference_arm(args, dist):
 
     n = 32
     rho, u = W.taylor_green(n, n, n, u0=0.05)
-    o = OracleSim("D3Q27", n, n, n, Params(tau=tgv_tau(args.n)))
+    o = OracleSim("D3Q27", n, n, n, Params(tau=tgv_tau(args.n), omega_bulk=OMEGA_BULK))
     o.init(torch.tensor(rho), torch.tensor(u))
     o.step(args.warmup)
     t0 = time.perf_counter()
@@ -350,13 +355,14 @@ def our_arm(args, dist):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"D3Q27 CM-LBM FP32 decaying Taylor-Green vortex {n}^3 periodic, u0=0.05, Re=1600, "
-                               f"no LES (tau={tgv_tau(n):.6f})",
+                               f"no LES (tau={tgv_tau(n):.6f}, bulk rate {OMEGA_BULK})",
                    "cells": N, "l2": "state 2 x %.2f GB >> 129 MB L2, no flush" % (27 * 4 * N / 1e9),
                    "parallelism": "replicas" if dist.world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"], "peak_kind": pk_kind,
                      "traffic": None if traffic_pc is None else traffic_pc * N,
-                     "algorithmic_bytes_per_cell": bpc, "kernel": "k_step<D3Q27,f32,periodic>"},
+                     "algorithmic_bytes_per_cell": bpc,
+                     "kernel": "k_step<D3Q27,f32,periodic>"},
         "clocks": ck,
         "gpu_launches": int(launches),
         "diagnostics": {"mass": red[0], "kinetic_energy": red[4]},

@@ -9,15 +9,15 @@
  * One step of the library (cmlbm_step) is, for every cell x:
  *   pull      g_i(x) = s_i(x - e_i)                    (standard streaming, Eq. cascadedstreaming1)
  *   moments   rho = sum g, rho u = sum g e + F/2        (Eqs. densitycalculation, velocitycalculation)
- *   central   kbar_a = sum g (e - u)^a                  (Sec. 6, transformed central moments)
+ *   central   kbar_a = sum g (e - u)^a                  (Sec. 7, transformed central moments)
  *   source    sigma_a by the exact hierarchical identity (Eq. centralmomentforceexactidentity2 with
  *             kappa = kbar + sigma/2, Eq. transformedcentralmoments)
  *   relax     post_a = kbar_a + omega_a (kappa^M_a - sigma_a/2 - kbar_a) + sigma_a
- *             (attractors Eq. centralmomenttransformed; procedure of Secs. 9-10)
- *   back      populations with the post-collision central moments (exact inverse, Sec. 8)
+ *             (attractors Eq. centralmomenttransformed; procedure of Secs. 10-11)
+ *   back      populations with the post-collision central moments (exact inverse, Sec. 9)
  *   store     s_i(x) <- post-collision population.
  * D3Q27, the Smagorinsky eddy viscosity, the boundaries and the storage formats are not in
- * the paper (it is written for D2Q9 and says the procedure extends to 3D, Secs. 2 and 13);
+ * the paper (it is written for D2Q9 and says the procedure extends to 3D, Secs. 2 and 15);
  * the readings used are stated at each field below.
  *
  * Conventions
@@ -65,6 +65,7 @@ enum { CMLBM_F64 = 0, CMLBM_F32 = 1, CMLBM_BF16 = 2, CMLBM_F16 = 3 }; /* state s
 enum { CMLBM_PERIODIC = 0, CMLBM_BOUNCEBACK = 1 };                 /* per-axis boundary */
 enum { CMLBM_DEVICE = 0, CMLBM_HOST = 1 };                         /* where a buffer lives */
 enum { CMLBM_ATTRACTOR_MAXWELL = 0, CMLBM_ATTRACTOR_FACTORIZED = 1 };
+enum { CMLBM_KERNEL_AUTO = 0, CMLBM_KERNEL_DIRECT = 1, CMLBM_KERNEL_TMA = 2 };
 
 typedef struct cmlbm cmlbm_t;
 
@@ -78,11 +79,11 @@ typedef struct cmlbm cmlbm_t;
  *                         crossed wall's velocity (the mean of both walls on an edge link).
  *   wall_velocity[a][s]   velocity of the wall on axis a, side s (0 = below index 0, 1 = above n-1).
  *   tau                   shear relaxation time: omega_nu = 1/tau, nu = c_s^2 (tau - 1/2)
- *                         (Sec. 9, text after Eq. collisionkernelg8). Must satisfy tau > 1/2.
+ *                         (Sec. 10, text after Eq. collisionkernelg8). Must satisfy tau > 1/2.
  *   omega_bulk            rate of the trace of the second-order central moments (omega_3 of
  *                         the paper); 0 = follow the (effective) shear rate.
  *   omega_3, omega_4      rates of the third-order and of the fourth- and higher-order central
- *                         moments (0 < omega < 2, Sec. 9).
+ *                         moments (0 < omega < 2, Sec. 10).
  *   smagorinsky_cs        Smagorinsky constant C_s; 0 disables the eddy viscosity. Reading
  *                         (paper silent on the model; frame invariance required by Sec. 1):
  *                         Pi = kappa_ij - c_s^2 rho delta_ij from second-order central moments,
@@ -91,11 +92,16 @@ typedef struct cmlbm cmlbm_t;
  *   van_driest_utau_over_nu  u_tau / nu_0 so that y+ = y_wall * u_tau / nu_0, y_wall = distance to
  *                         the nearest y wall (j + 1/2 or ny - 1/2 - j).
  *   attractor             CMLBM_ATTRACTOR_MAXWELL (Eq. centralmomenttransformed) or
- *                         CMLBM_ATTRACTOR_FACTORIZED (Sec. 11, Eq. factorxxyyfinal).
- *   reduced_compressibility  1 = momentum rho0 u = sum fbar e + F/2 (Sec. 10).
+ *                         CMLBM_ATTRACTOR_FACTORIZED (Sec. 13, Eq. factorxxyyfinal).
+ *   reduced_compressibility  1 = momentum rho0 u = sum fbar e + F/2 (Sec. 12).
  *   rho0                  reference density of the reduced-compressibility form.
  *   stream                cudaStream_t to launch on; NULL = the legacy default stream.
  *   device                CUDA device ordinal the handle lives on.
+ *   kernel                step kernel: CMLBM_KERNEL_AUTO (currently the direct-load kernel, the
+ *                         faster one measured), CMLBM_KERNEL_DIRECT, or CMLBM_KERNEL_TMA (rows staged
+ *                         in shared memory by TMA; error when the configuration cannot use it). The
+ *                         TMA path covers D3Q27 with FP32 / BF16 / FP16 storage, nx a multiple of
+ *                         128, the Maxwellian attractor and standard compressibility.
  */
 typedef struct {
     int lattice;
@@ -115,6 +121,7 @@ typedef struct {
     double rho0;
     void* stream;
     int device;
+    int kernel;
 } cmlbm_config;
 
 /* Defaults: D3Q27, 32^3, FP32, periodic, tau = 0.8, omega_bulk = 0, omega_3 = omega_4 = 1,
@@ -166,7 +173,8 @@ CMLBM_API int cmlbm_moments_of(cmlbm_t* h, const void* state, double* rho, doubl
 
 /* FP64 reductions of the current field: out = {sum rho, sum rho u_x, sum rho u_y,
  * sum rho u_z, sum rho |u|^2 / 2} (host array, synchronous, deterministic order).
- * Returns CMLBM_ERR_DIVERGED if any of them is not finite. */
+ * Returns CMLBM_ERR_DIVERGED if any of them is not finite, and CMLBM_ERR_CUDA if a TMA-staged
+ * step since the last check gave up on a bounded pipeline wait (its output is then invalid). */
 CMLBM_API int cmlbm_reduce(cmlbm_t* h, double out[5]);
 
 /* Bytes of one state buffer (Q * N * storage size). */
@@ -176,6 +184,20 @@ CMLBM_API size_t cmlbm_state_bytes(const cmlbm_t* h);
  * cmlbm_state_bytes). */
 CMLBM_API int cmlbm_get_state(cmlbm_t* h, void* dst, size_t bytes, int where);
 CMLBM_API int cmlbm_set_state(cmlbm_t* h, const void* src, size_t bytes, int where);
+
+/* ---- turbulence as forcing (Sec. 14, filtered kinetic equation) -------------------------- *
+ * The unresolved stresses act as the body force F = rho a', a'_i = -d_j (u'_i u'_j), with the
+ * resolved momentum rho0 u = sum fbar e + rho a' / 2 (Eq. resolvedvelocitycalculation; configure
+ * reduced_compressibility = 1 and, as the paper suggests, the factorized attractor). Closure
+ * (paper: any conventional macroscopic model): Smagorinsky, u'_i u'_j (deviatoric) = -2 nu_t S_ij,
+ * nu_t = cs^2 |S|, |S| = sqrt(2 S:S), S from second-order central differences of the resolved
+ * velocity of the current field (computed with the force in place), lattice spacing 1.
+ * cmlbm_turbulence_force sets the handle's force field to rho a' plus the uniform force last
+ * given to cmlbm_set_force; cmlbm_step_filtered repeats {turbulence_force; step} nsteps times.
+ * Periodic boundaries only (CMLBM_ERR_UNSUPPORTED otherwise). Allocates 13 N arithmetic values
+ * of scratch and force field on first use. */
+CMLBM_API int cmlbm_turbulence_force(cmlbm_t* h, double cs);
+CMLBM_API int cmlbm_step_filtered(cmlbm_t* h, int nsteps, double cs);
 
 /* ---- adjoint (reverse mode of cmlbm_step_buffers; paper silent) ---------------------- *
  * Adjoint state lambda is [Q][N] in the arithmetic precision (FP64 for F64 storage, FP32
@@ -195,6 +217,7 @@ CMLBM_API int cmlbm_step_adjoint(cmlbm_t* h, const void* state, const void* lamb
 
 /* Kernel launches issued by the handle so far (for benchmark accounting). */
 CMLBM_API long long cmlbm_launch_count(const cmlbm_t* h);
+
 
 #ifdef __cplusplus
 }

@@ -9,9 +9,9 @@ with it; the product path fails loudly when the CUDA library is missing.
 
 Modules
   lattice    velocity sets, rest weights, monomial orders, orthogonal basis K (Sec. 2)
-  moments    raw and central moments, binomial frame shift, exact inverse (Secs. 6, 8)
-  collision  hydrodynamics, source central moments, attractors, relaxation (Secs. 4-9)
-  literal    the element-wise D2Q9 collision exactly as printed (Secs. 8-10)
+  moments    raw and central moments, binomial frame shift, exact inverse (Secs. 7, 9)
+  collision  hydrodynamics, source central moments, attractors, relaxation (Secs. 4-10)
+  literal    the element-wise D2Q9 collision exactly as printed (Secs. 9-11)
   les        Smagorinsky eddy viscosity from the non-equilibrium stress (paper silent)
   stream     pull streaming, periodic and half-way bounce-back walls, initial state
   solver     the time loop, diagnostics and the configurations

@@ -2,21 +2,21 @@
 
 Test infrastructure (see the package docstring).
 
-One collision, in the paper's order (Secs. 6-10):
+One collision, in the paper's order (Secs. 6-11):
   1. rho = sum fbar, rho u = sum fbar e + F/2          (Eqs. densitycalculation, velocitycalculation)
   2. kbar_a = central moments of fbar about u          (definition below Eq. centralmomentforcing)
   3. sigma_a from the exact hierarchical identity      (Eq. centralmomentforceexactidentity2 with
      kappa = kbar + sigma/2, Eq. transformedcentralmoments; kappa_0 = rho, kappa_x = 0 as
-     stated under the relations of Sec. 7)
+     stated under the relations of Sec. 8)
   4. attractor kbar^M_a = kappa^M_a - sigma_a/2        (Eq. centralmomenttransformed)
   5. relax the non-conserved moments toward the attractor and add the source:
-     post_a = kbar_a + omega_a (kbar^M_a - kbar_a) + sigma_a   (Sec. 9 procedure; Eq. cascadedcollision1)
-  6. back to populations through the exact inverse (Sec. 8).
+     post_a = kbar_a + omega_a (kbar^M_a - kbar_a) + sigma_a   (Sec. 10 procedure; Eq. cascadedcollision1)
+  6. back to populations through the exact inverse (Sec. 9).
 The element-wise D2Q9 formulas as printed live in ``literal.py``; where they differ from
 this form at third and fourth order in the force, this form is the normative reading
 (it follows the stated principle: relax toward Eq. centralmomenttransformed, then add S).
 
-Rates (Sec. 9, below Eq. collisionkernelg8): the trace of the second-order moments relaxes
+Rates (Sec. 10, below Eq. collisionkernelg8): the trace of the second-order moments relaxes
 with the bulk rate, the deviatoric and off-diagonal second-order moments with the shear
 rate omega_nu = 1/tau (nu = c_s^2 (1/omega_nu - 1/2)); third order with omega3, fourth and
 higher with omega4. Where the eddy viscosity is on, omega_nu comes from ``les.py``.
@@ -37,15 +37,15 @@ class Params:
     omega3: float = 1.0            # third-order central moments
     omega4: float = 1.0            # fourth and higher orders
     cs_smag: float = 0.0           # Smagorinsky constant, 0 = no eddy viscosity
-    attractor: str = "maxwell"     # "maxwell" (Eq. centralmomenttransformed) or "factorized" (Sec. 11)
-    reduced_compressibility: bool = False   # Sec. 10: rho0 u = sum fbar e + F/2
+    attractor: str = "maxwell"     # "maxwell" (Eq. centralmomenttransformed) or "factorized" (Sec. 13)
+    reduced_compressibility: bool = False   # Sec. 12: rho0 u = sum fbar e + F/2
     rho0: float = 1.0
 
 
 def hydrodynamics(fbar, F, lat, p=None):
     """rho = sum fbar (Eq. densitycalculation); rho u = sum fbar e + F/2 (Eq. velocitycalculation).
 
-    With reduced compressibility (Sec. 10) the momentum is rho0 u instead of rho u.
+    With reduced compressibility (Sec. 12) the momentum is rho0 u instead of rho u.
     """
     rho = fbar.sum(0)
     mom = []
@@ -80,13 +80,13 @@ def maxwell_central(rho, lat):
 
 
 def source_central(kbar, rho, F, lat):
-    """Central moments sigma_a of the source, in increasing order (Sec. 5 and Sec. 7).
+    """Central moments sigma_a of the source, in increasing order (Sec. 5 and Sec. 8).
 
     The exact identity Gamma_(x^m y^n) = m (F_x/rho) Pi_(x^(m-1) y^n) + n (F_y/rho) Pi_(x^m y^(n-1))
     (Eq. centralmomentforceexactidentity2), with a third term in 3D, applied to the central
     moments kappa of the untransformed f, kappa_a = kbar_a + sigma_a / 2 (Eq.
     transformedcentralmoments). The conserved central moments are kappa_0 = rho and
-    kappa_x = kappa_y = kappa_z = 0 by definition (Sec. 7, text above the reduced
+    kappa_x = kappa_y = kappa_z = 0 by definition (Sec. 8, text above the reduced
     relations), which gives sigma_x = F_x and zero second-order sources (Eq.
     centralmomentforcingtransformed).
 
@@ -118,7 +118,7 @@ def equilibrium(rho, u, F, lat):
     """Initial transformed populations fbar = f^M - S/2 with the Maxwellian moments.
 
     The discrete Maxwellian is the population whose central moments are kappa^M (matching
-    principle, Sec. 6). Its source is the identity evaluated at kappa = kappa^M (the special
+    principle, Sec. 7). Its source is the identity evaluated at kappa = kappa^M (the special
     case noted under Eq. exactidentitycomponents). Initialisation itself is paper silent.
     """
     kM = maxwell_central(rho, lat)
@@ -137,7 +137,7 @@ def equilibrium(rho, u, F, lat):
 
 
 def _factorized_attractor(kM, post2, rho, lat):
-    """Factorized attractors (Sec. 11): products of post-collision second-order central moments.
+    """Factorized attractors (Sec. 13): products of post-collision second-order central moments.
 
     D2Q9: kappa^at_xxy = kappa^at_xyy = 0 and kappa^at_xxyy = k~_xx k~_yy (Eq. factorxxyy).
     Reading: the product is divided by rho so that it equals the Maxwellian rho c_s^4 when the
@@ -228,7 +228,7 @@ def collide(fbar, F, lat, p, cs_eff=None):
 
 
 def source_populations(fbar, F, lat, p=None):
-    """S_alpha: the populations whose central moments about u are sigma (Sec. 8, S = K D^-1 m^s)."""
+    """S_alpha: the populations whose central moments about u are sigma (Sec. 9, S = K D^-1 m^s)."""
     rho, u = hydrodynamics(fbar, F, lat, p)
     kbar = M.central_moments(fbar, u, lat)
     sigma, _ = source_central(kbar, rho, F, lat)

@@ -6,7 +6,7 @@ D2Q9 follows the paper's numbering (Sec. 2, Eq. velocityd2q9, with the direction
 fixed by the columns of the basis vectors |e_x>, |e_y>):
   0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1).
 D3Q27 (paper silent; the paper says the procedure extends to three dimensions, Sec. 2
-and Sec. 13) uses the lexicographic order i = 9*(ez+1) + 3*(ey+1) + (ex+1).
+and Sec. 15) uses the lexicographic order i = 9*(ez+1) + 3*(ey+1) + (ex+1).
 
 The orthogonal basis K for D2Q9 is built from the Gram-Schmidt combinations of
 monomials printed in Sec. 2 (Eq. collisionmatrix1 and the list above it). For D3Q27 the

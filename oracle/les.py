@@ -3,10 +3,10 @@
 Test infrastructure (see the package docstring).
 
 Paper silent on the formula: the paper asks that sub-grid models be inertial-frame invariant
-(Sec. 1) and routes turbulence models through the filtered kinetic equation (Sec. 12). The
+(Sec. 1) and routes turbulence models through the filtered kinetic equation (Sec. 14). The
 reading used here takes the non-equilibrium stress from second-order CENTRAL moments,
     Pi^neq_ij = kappa_ij - c_s^2 rho delta_ij,
-which carry no F.u terms (second-order kappa of f equals that of fbar, Sec. 7), so the
+which carry no F.u terms (second-order kappa of f equals that of fbar, Sec. 8), so the
 eddy viscosity does not depend on the frame. With Delta = 1 and
     S_ij = -Pi^neq_ij / (2 rho c_s^2 tau_eff),   |S| = sqrt(2 S:S),
     tau_eff = tau_0 + 3 nu_t,   nu_t = (C_s Delta)^2 |S|,

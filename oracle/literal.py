@@ -1,4 +1,4 @@
-"""The D2Q9 collision exactly as printed, element by element (Secs. 8-10).
+"""The D2Q9 collision exactly as printed, element by element (Secs. 9-11).
 
 Test infrastructure (see the package docstring). This is a regression form; the normative
 step is ``collision.collide``. Readings of the printed text:
@@ -12,10 +12,13 @@ All arrays are float64 tensors with a trailing cell shape; F has at least two co
 import torch
 
 
-def collide_literal(fb, F, omega, sigma_central_in_g67=False):
-    """Post-collision fbar by Eqs. collisionkernelg3-g8 and the element-wise update of Sec. 10.
+def collide_literal(fb, F, omega, sigma_central_in_g67=False, rho0=None, factorized=False):
+    """Post-collision fbar by Eqs. collisionkernelg3-g8 and the element-wise update of Sec. 11.
 
     fb[9, ...] in the paper's direction order, F[>=2, ...], omega = (w3, w4, w5, w6, w7, w8).
+    rho0: when given, the reduced-compressibility kernels of Sec. 12 (Eqs.
+    collisionkernelcompact3-8) with rho0 u = sum fbar e + F/2. factorized: g8 with the
+    factorized attractor of Sec. 13 (Eq. factorxxyyfinal, product as printed) in place of rho/9.
     Returns (fbar_post, g, S) with g = (g3..g8) and S[9, ...] (Eqs. vsourceterms0-8).
     """
     w3, w4, w5, w6, w7, w8 = omega
@@ -26,8 +29,15 @@ def collide_literal(fb, F, omega, sigma_central_in_g67=False):
     rho = f0 + f1 + f2 + f3 + f4 + f5 + f6 + f7 + f8
     kx_r = f1 - f3 + f5 - f6 - f7 + f8
     ky_r = f2 - f4 + f5 + f6 - f7 - f8
-    ux = (kx_r + 0.5 * Fx) / rho
-    uy = (ky_r + 0.5 * Fy) / rho
+    den = rho if rho0 is None else rho0
+    ux = (kx_r + 0.5 * Fx) / den
+    uy = (ky_r + 0.5 * Fy) / den
+    # density factors of the kernels: rho (Sec. 10) or (rho0 - drho), (2 rho0 - drho), (3 rho0 - drho)
+    if rho0 is None:
+        r1 = r2 = r3 = rho
+    else:
+        drho = rho - rho0
+        r1, r2, r3 = rho0 - drho, 2 * rho0 - drho, 3 * rho0 - drho
 
     # Eqs. rawmomenttransformed3-8 with the direction subsets A3..A8, B5..B7
     kxx_r = f1 + f3 + f5 + f6 + f7 + f8
@@ -89,22 +99,32 @@ def collide_literal(fb, F, omega, sigma_central_in_g67=False):
     else:
         sg6, sg7 = s_xxy, s_xyy
 
-    # Eqs. collisionkernelg3-g8
-    g3 = w3 / 12.0 * (2.0 / 3.0 * rho + rho * (ux * ux + uy * uy) - (kxx_r + kyy_r) - 0.5 * (s_xx + s_yy))
-    g4 = w4 / 4.0 * (rho * (ux * ux - uy * uy) - (kxx_r - kyy_r) - 0.5 * (s_xx - s_yy))
-    g5 = w5 / 4.0 * (rho * ux * uy - kxy_r - 0.5 * s_xy)
-    g6 = (w6 / 4.0 * (2 * rho * ux * ux * uy + kxxy_r - 2 * ux * kxy_r - uy * kxx_r - 0.5 * sg6)
+    # Eqs. collisionkernelg3-g8 (Eqs. collisionkernelcompact3-8 with rho0)
+    g3 = w3 / 12.0 * (2.0 / 3.0 * rho + r1 * (ux * ux + uy * uy) - (kxx_r + kyy_r) - 0.5 * (s_xx + s_yy))
+    g4 = w4 / 4.0 * (r1 * (ux * ux - uy * uy) - (kxx_r - kyy_r) - 0.5 * (s_xx - s_yy))
+    g5 = w5 / 4.0 * (r1 * ux * uy - kxy_r - 0.5 * s_xy)
+    g6 = (w6 / 4.0 * ((r2 if rho0 is not None else 2 * rho) * ux * ux * uy + kxxy_r - 2 * ux * kxy_r - uy * kxx_r
+                      - 0.5 * sg6)
           - 0.5 * uy * (3 * g3 + g4) - 2 * ux * g5)
-    g7 = (w7 / 4.0 * (2 * rho * ux * uy * uy + kxyy_r - 2 * uy * kxy_r - ux * kyy_r - 0.5 * sg7)
+    g7 = (w7 / 4.0 * ((r2 if rho0 is not None else 2 * rho) * ux * uy * uy + kxyy_r - 2 * uy * kxy_r - ux * kyy_r
+                      - 0.5 * sg7)
           - 0.5 * ux * (3 * g3 - g4) - 2 * uy * g5)
-    g8 = (w8 / 4.0 * (rho / 9.0 + 3 * rho * ux * ux * uy * uy
+    if factorized:
+        # Eq. factorxxyyfinal (and its reduced-compressibility form)
+        att = ((kxx_r - r1 * ux * ux + Fx * ux + (6 * g3 + 2 * g4))
+               * (kyy_r - r1 * uy * uy + Fy * uy + (6 * g3 - 2 * g4))
+               - Fx / rho * kxyy - Fy / rho * kxxy - Fy * Fy / (2 * rho ** 2) * kxx - Fx * Fx / (2 * rho ** 2) * kyy
+               - 2 * Fx * Fy / rho ** 2 * kxy)
+    else:
+        att = rho / 9.0
+    g8 = (w8 / 4.0 * (att + (r3 if rho0 is not None else 3 * rho) * ux * ux * uy * uy
                       - (kxxyy_r - 2 * ux * kxyy_r - 2 * uy * kxxy_r + ux * ux * kyy_r + uy * uy * kxx_r
                          + 4 * ux * uy * kxy_r)
                       - 0.5 * s_xxyy)
           - 2 * g3 - 0.5 * uy * uy * (3 * g3 + g4) - 0.5 * ux * ux * (3 * g3 - g4)
           - 4 * ux * uy * g5 - 2 * uy * g6 - 2 * ux * g7)
 
-    # element-wise update of Sec. 10 (g0 = g1 = g2 = 0, collision invariants)
+    # element-wise update of Sec. 11 (g0 = g1 = g2 = 0, collision invariants)
     post = torch.stack([
         f0 + (-4 * (g3 - g8)) + S[0],
         f1 + (-g3 + g4 + 2 * (g7 - g8)) + S[1],

@@ -13,7 +13,7 @@ from .lattice import DT
 
 
 def raw_moments(f, lat):
-    """kappa'_a = sum_alpha f_alpha e_x^a0 e_y^a1 e_z^a2 (Sec. 8, Eq. rawmomentdistributionfunction1)."""
+    """kappa'_a = sum_alpha f_alpha e_x^a0 e_y^a1 e_z^a2 (Sec. 9, Eq. rawmomentdistributionfunction1)."""
     out = []
     for (a0, a1, a2) in lat.monomials:
         acc = torch.zeros_like(f[0])
@@ -29,7 +29,7 @@ def raw_moments(f, lat):
 def central_moments(f, u, lat):
     """kappa_a = sum_alpha f_alpha (e_x-u_x)^a0 (e_y-u_y)^a1 (e_z-u_z)^a2.
 
-    Definition of Sec. 6 (Eqs. centralmomentdistributionfunction1 and the transformed
+    Definition of Sec. 7 (Eqs. centralmomentdistributionfunction1 and the transformed
     version below Eq. centralmomentforcing), written out as an explicit sum over the
     directions; the third factor is the three-dimensional reading.
     """
@@ -51,7 +51,7 @@ def central_moments(f, u, lat):
 
 
 def central_to_raw(kappa, u, lat):
-    """Binomial theorem of Sec. 8 (Eq. binomialtheorem), used in the rest-frame direction.
+    """Binomial theorem of Sec. 9 (Eq. binomialtheorem), used in the rest-frame direction.
 
     Since e = (e - u) + u, the raw moment of exponent a is
         kappa'_a = sum_{b <= a} prod_d C(a_d, b_d) u_d^(a_d - b_d) kappa_b.
@@ -77,7 +77,7 @@ def central_to_raw(kappa, u, lat):
 
 
 def raw_to_populations(raw, lat):
-    """Exact inverse through the orthogonal basis (Sec. 8, below Eq. sourceformulation1).
+    """Exact inverse through the orthogonal basis (Sec. 9, below Eq. sourceformulation1).
 
     The projections <K_beta|f> are combinations of raw monomial moments with the
     coefficients that define K_beta; then f = K D^-1 (K^T f) with D = diag(<K_beta|K_beta>).

@@ -13,6 +13,7 @@ from .lattice import DT, get as get_lattice
 from . import collision as C
 from . import stream as ST
 from . import les as L
+from . import filtered as FL
 
 
 class OracleSim:
@@ -37,19 +38,20 @@ class OracleSim:
 
     # ---- set-up -------------------------------------------------------------------
     def set_force(self, uniform=(0.0, 0.0, 0.0), field=None):
+        self.F_uniform = torch.zeros((3,) + self.shape, dtype=DT)
+        for d in range(3):
+            self.F_uniform[d] += float(uniform[d])
         if field is not None:
             self.F = torch.as_tensor(field, dtype=DT).reshape((3,) + self.shape).clone()
         else:
-            self.F = torch.zeros((3,) + self.shape, dtype=DT)
-            for d in range(3):
-                self.F[d] += float(uniform[d])
+            self.F = self.F_uniform.clone()
 
     def init(self, rho=None, u=None):
         """Pre-collision field fbar = f^M(rho, u) - S/2 (paper silent on initialisation)."""
         rho = torch.ones(self.shape, dtype=DT) if rho is None else torch.as_tensor(rho, dtype=DT).reshape(self.shape)
         u = torch.zeros((3,) + self.shape, dtype=DT) if u is None else torch.as_tensor(u, dtype=DT).reshape((3,) + self.shape)
         if self.p.reduced_compressibility:
-            # Sec. 10: the momentum is rho0 u, so the equilibrium is centred on rho0 u / rho
+            # Sec. 12: the momentum is rho0 u, so the equilibrium is centred on rho0 u / rho
             u = u * (self.p.rho0 / rho)
         fbar = C.equilibrium(rho, u, self.F, self.lat)
         self.s = ST.unstream(fbar, self.lat, self.bc, self.uw)
@@ -65,6 +67,19 @@ class OracleSim:
         for _ in range(n):
             g = self.pre_collision()
             self.s = C.collide(g, self.F, self.lat, self.p, self.cs_eff)
+
+    def turbulence_force(self, cs):
+        """Set F = rho a' from the Smagorinsky closure of the current resolved field (Sec. 14)."""
+        if any(b != ST.PERIODIC for b in self.bc):
+            raise ValueError("turbulence forcing needs periodic boundaries")
+        rho, u = self.moments()
+        base = getattr(self, "F_uniform", torch.zeros_like(self.F))
+        self.F = rho * FL.turbulence_acceleration(u, cs, self.lat.d) + base
+
+    def step_filtered(self, n, cs):
+        for _ in range(n):
+            self.turbulence_force(cs)
+            self.step(1)
 
     # ---- diagnostics --------------------------------------------------------------
     def moments(self):

@@ -28,7 +28,8 @@ BCS = {"periodic": PERIODIC, "bounceback": BOUNCEBACK}
 SYMBOLS = ["cmlbm_config_default", "cmlbm_create", "cmlbm_destroy", "cmlbm_last_error", "cmlbm_set_stream",
            "cmlbm_set_force", "cmlbm_init", "cmlbm_step", "cmlbm_step_buffers", "cmlbm_moments",
            "cmlbm_moments_of", "cmlbm_reduce", "cmlbm_state_bytes", "cmlbm_get_state", "cmlbm_set_state",
-           "cmlbm_adjoint_terminal", "cmlbm_step_adjoint", "cmlbm_launch_count"]
+           "cmlbm_adjoint_terminal", "cmlbm_step_adjoint", "cmlbm_launch_count",
+           "cmlbm_turbulence_force", "cmlbm_step_filtered"]
 
 
 class Config(ctypes.Structure):
@@ -50,6 +51,7 @@ class Config(ctypes.Structure):
         ("rho0", ctypes.c_double),
         ("stream", ctypes.c_void_p),
         ("device", ctypes.c_int),
+        ("kernel", ctypes.c_int),
     ]
 
 
@@ -90,6 +92,8 @@ def load():
         "cmlbm_adjoint_terminal": (I, [P, P, P, P, P, P]),
         "cmlbm_step_adjoint": (I, [P, P, P, P, P]),
         "cmlbm_launch_count": (ctypes.c_longlong, [P]),
+        "cmlbm_turbulence_force": (I, [P, ctypes.c_double]),
+        "cmlbm_step_filtered": (I, [P, I, ctypes.c_double]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -118,7 +122,7 @@ def _as_vec3(v):
 
 def make_config(lattice="D3Q27", nx=32, ny=32, nz=32, storage="f32", bc=("periodic",) * 3, wall_velocity=None,
                 tau=0.8, omega_bulk=0.0, omega_3=1.0, omega_4=1.0, smagorinsky_cs=0.0, van_driest=None,
-                attractor="maxwell", reduced_compressibility=False, rho0=1.0, device=0, stream=None):
+                attractor="maxwell", reduced_compressibility=False, rho0=1.0, device=0, stream=None, kernel="auto"):
     lib = load()
     c = Config()
     lib.cmlbm_config_default(ctypes.byref(c))
@@ -144,6 +148,7 @@ def make_config(lattice="D3Q27", nx=32, ny=32, nz=32, storage="f32", bc=("period
     c.rho0 = float(rho0)
     c.device = int(device)
     c.stream = stream
+    c.kernel = {"auto": 0, "direct": 1, "tma": 2}[kernel] if isinstance(kernel, str) else int(kernel)
     return c
 
 
@@ -156,6 +161,8 @@ class Solver:
 
     def __init__(self, **kw):
         self.lib = load()
+        if "device" not in kw and torch.cuda.is_available():
+            kw["device"] = torch.cuda.current_device()
         if kw.get("stream") is None and torch.cuda.is_available():
             kw["stream"] = ctypes.c_void_p(torch.cuda.current_stream(kw.get("device", 0)).cuda_stream)
         self.cfg = make_config(**kw)
@@ -218,6 +225,13 @@ class Solver:
 
     def step(self, n=1):
         self._check(self.lib.cmlbm_step(self.h, int(n)))
+
+    def turbulence_force(self, cs):
+        """Set the force field to rho a' from the Smagorinsky closure (filtered equation)."""
+        self._check(self.lib.cmlbm_turbulence_force(self.h, float(cs)))
+
+    def step_filtered(self, n, cs):
+        self._check(self.lib.cmlbm_step_filtered(self.h, int(n), float(cs)))
 
     def step_buffers(self, src, dst):
         self._check(self.lib.cmlbm_step_buffers(self.h, _ptr(src), _ptr(dst)))

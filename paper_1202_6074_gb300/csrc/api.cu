@@ -28,6 +28,12 @@ struct cmlbm {
     cudaStream_t st = nullptr;
     long long launches = 0;
     std::string err;
+    // TMA-staged step: tensor maps of the two state buffers ({main, halo} each, 128 B apiece)
+    bool tma = false;
+    alignas(128) unsigned char maps[2][2][128];
+    int* flag = nullptr;       // device error flag of the bounded pipeline waits
+    int nsm = 0;
+    void* turb = nullptr;      // [10][N] arithmetic type: rho, u, eddy stress (turbulence forcing)
 };
 
 namespace {
@@ -90,8 +96,24 @@ cudaError_t dispatch(const cmlbm* h, Fn&& fn) {
     return cudaErrorInvalidValue;
 }
 
+// TMA-staged step when the handle has maps for src (one of its buffers, or maps made here).
+cudaError_t do_step_tma(cmlbm* h, const void* map_main, const void* map_halo, const void* src, void* dst) {
+    switch (h->cfg.storage) {
+        case CMLBM_F32: return cm::launch_step_tma<float>(map_main, map_halo, src, dst, h->force, h->p, h->flag, h->nsm, h->st);
+        case CMLBM_BF16: return cm::launch_step_tma<__nv_bfloat16>(map_main, map_halo, src, dst, h->force, h->p, h->flag, h->nsm, h->st);
+        case CMLBM_F16: return cm::launch_step_tma<__half>(map_main, map_halo, src, dst, h->force, h->p, h->flag, h->nsm, h->st);
+    }
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t do_step(cmlbm* h, const void* src, void* dst) {
     ++h->launches;
+    if (h->tma) {
+        for (int k = 0; k < 2; ++k)
+            if (src == h->buf[k]) return do_step_tma(h, h->maps[k][0], h->maps[k][1], src, dst);
+        alignas(128) unsigned char m[2][128];
+        if (cm::encode_tma_maps(src, h->p, h->cfg.storage, m[0], m[1])) return do_step_tma(h, m[0], m[1], src, dst);
+    }
     return dispatch(h, [&](auto d, auto* s) {
         using S = std::remove_pointer_t<decltype(s)>;
         return cm::launch_step<decltype(d)::value, S>(src, dst, h->force, h->p, h->st);
@@ -213,10 +235,25 @@ int cmlbm_create(const cmlbm_config* cfg, cmlbm_t** out) {
         }
     }
     if (cudaMalloc(&h->part, sizeof(double) * 5 * cm::kReduceMaxBlocks) != cudaSuccess ||
-        cudaMalloc(&h->red, sizeof(double) * 5) != cudaSuccess) {
+        cudaMalloc(&h->red, sizeof(double) * 5) != cudaSuccess || cudaMalloc(&h->flag, sizeof(int)) != cudaSuccess ||
+        cudaMemset(h->flag, 0, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         cmlbm_destroy(h);
         return fail(nullptr, CMLBM_ERR_NOMEM, "cudaMalloc of the reduction buffers failed");
+    }
+    if (cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess) h->nsm = 1;
+    if (c.kernel == CMLBM_KERNEL_TMA) {
+        const bool eligible = h->D == 3 && c.storage != CMLBM_F64 && c.attractor == CMLBM_ATTRACTOR_MAXWELL &&
+                              !c.reduced_compressibility;
+        bool ok = eligible;
+        for (int k = 0; k < 2 && ok; ++k) ok = cm::encode_tma_maps(h->buf[k], p, c.storage, h->maps[k][0], h->maps[k][1]);
+        h->tma = ok;
+        if (!ok && c.kernel == CMLBM_KERNEL_TMA) {
+            cmlbm_destroy(h);
+            return fail(nullptr, CMLBM_ERR_UNSUPPORTED,
+                        "the TMA-staged step needs D3Q27, FP32/BF16/FP16 storage, nx a multiple of 128 and the "
+                        "standard collision");
+        }
     }
     int rc = cmlbm_init(h, nullptr, nullptr, CMLBM_DEVICE);
     if (rc != CMLBM_OK) {
@@ -243,6 +280,8 @@ void cmlbm_destroy(cmlbm_t* h) {
     cudaFree(h->part);
     cudaFree(h->red);
     cudaFree(h->stage);
+    cudaFree(h->flag);
+    cudaFree(h->turb);
     delete h;
 }
 
@@ -396,6 +435,15 @@ int cmlbm_reduce(cmlbm_t* h, double out[5]) {
     if (e != cudaSuccess) return cuda_fail(h, e, "reduction download");
     e = cudaStreamSynchronize(h->st);
     if (e != cudaSuccess) return cuda_fail(h, e, "reduction");
+    if (h->tma) {
+        int flag = 0;
+        e = cudaMemcpy(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(h, e, "pipeline flag");
+        if (flag) {
+            cudaMemset(h->flag, 0, sizeof(int));
+            return fail(h, CMLBM_ERR_CUDA, "a TMA-staged step gave up on a bounded pipeline wait");
+        }
+    }
     for (int k = 0; k < 5; ++k)
         if (!std::isfinite(out[k])) return fail(h, CMLBM_ERR_DIVERGED, "non-finite value in the reductions");
     return CMLBM_OK;
@@ -422,6 +470,45 @@ int cmlbm_set_state(cmlbm_t* h, const void* src, size_t bytes, int where) {
                                                                                    : cudaMemcpyDeviceToDevice, h->st);
     if (e != cudaSuccess) return cuda_fail(h, e, "state copy");
     if (where == CMLBM_HOST && (e = cudaStreamSynchronize(h->st)) != cudaSuccess) return cuda_fail(h, e, "state copy");
+    return CMLBM_OK;
+}
+
+int cmlbm_turbulence_force(cmlbm_t* h, double cs) {
+    if (!h) return CMLBM_ERR_INVALID;
+    if (!(cs >= 0.0) || !std::isfinite(cs)) return fail(h, CMLBM_ERR_INVALID, "cs must be finite and >= 0");
+    if (h->p.bc[0] || h->p.bc[1] || h->p.bc[2])
+        return fail(h, CMLBM_ERR_UNSUPPORTED, "turbulence forcing needs periodic boundaries");
+    DeviceGuard g(h->cfg.device);
+    const size_t N = (size_t)h->p.N;
+    if (!h->force && cudaMalloc(&h->force, h->rsize * 3 * N) != cudaSuccess) {
+        h->force = nullptr;
+        cudaGetLastError();
+        return fail(h, CMLBM_ERR_NOMEM, "cudaMalloc of the force field failed");
+    }
+    if (!h->turb && cudaMalloc(&h->turb, h->rsize * 10 * N) != cudaSuccess) {
+        h->turb = nullptr;
+        cudaGetLastError();
+        return fail(h, CMLBM_ERR_NOMEM, "cudaMalloc of the turbulence scratch failed");
+    }
+    h->launches += 3;
+    cudaError_t e = dispatch(h, [&](auto d, auto* s) {
+        using S = std::remove_pointer_t<decltype(s)>;
+        return cm::launch_turbulence_force<decltype(d)::value, S>(h->buf[h->cur], h->force, h->p, cs, h->turb, h->st);
+    });
+    if (e != cudaSuccess) return cuda_fail(h, e, "turbulence forcing kernels");
+    h->p.has_field = 1;
+    return CMLBM_OK;
+}
+
+int cmlbm_step_filtered(cmlbm_t* h, int nsteps, double cs) {
+    if (!h) return CMLBM_ERR_INVALID;
+    if (nsteps < 0) return fail(h, CMLBM_ERR_INVALID, "nsteps must be >= 0");
+    for (int k = 0; k < nsteps; ++k) {
+        int rc = cmlbm_turbulence_force(h, cs);
+        if (rc) return rc;
+        rc = cmlbm_step(h, 1);
+        if (rc) return rc;
+    }
     return CMLBM_OK;
 }
 

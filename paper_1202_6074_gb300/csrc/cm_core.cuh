@@ -9,7 +9,7 @@
 // moments of h about u. The central moments of the weights about u are the products
 // prod_d c_{a_d}(u_d) with c_0 = 1, c_1 = -u, c_2 = 1/3 + u^2, so every quantity the kernel
 // rounds is O(u, drho, F) rather than O(1). The algebra is exact: it is the same step as the
-// paper's (Secs. 6-10) with the weights' moments moved out analytically.
+// paper's (Secs. 7-11) with the weights' moments moved out analytically.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -157,11 +157,13 @@ template <class S> struct Codec;
 template <> struct Codec<double> {
     using R = double;
     static __device__ __forceinline__ R ld(const double* p) { return __ldg(p); }
+    static __device__ __forceinline__ R ld_shared(const double* p) { return *p; }
     static __device__ __forceinline__ void st(double* p, R v) { *p = v; }
 };
 template <> struct Codec<float> {
     using R = float;
     static __device__ __forceinline__ R ld(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ R ld_shared(const float* p) { return *p; }
     static __device__ __forceinline__ void st(float* p, R v) { *p = v; }
 };
 template <> struct Codec<__nv_bfloat16> {
@@ -169,12 +171,18 @@ template <> struct Codec<__nv_bfloat16> {
     static __device__ __forceinline__ R ld(const __nv_bfloat16* p) {
         return __bfloat162float(__ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short*>(p))));
     }
+    static __device__ __forceinline__ R ld_shared(const __nv_bfloat16* p) {
+        return __bfloat162float(__ushort_as_bfloat16(*reinterpret_cast<const unsigned short*>(p)));
+    }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, R v) { *p = __float2bfloat16_rn(v); }
 };
 template <> struct Codec<__half> {
     using R = float;
     static __device__ __forceinline__ R ld(const __half* p) {
         return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(p))));
+    }
+    static __device__ __forceinline__ R ld_shared(const __half* p) {
+        return __half2float(__ushort_as_half(*reinterpret_cast<const unsigned short*>(p)));
     }
     static __device__ __forceinline__ void st(__half* p, R v) { *p = __float2half_rn(v); }
 };
@@ -207,7 +215,7 @@ template <class R> __device__ __forceinline__ void inv1(R& a, R& b, R& c, R u, R
 // Pull with periodic wrap and half-way bounce-back; fills h (deviation populations, slot order)
 // ------------------------------------------------------------------------------------------
 template <int D, class S, bool WALLS>
-__device__ __forceinline__ void gather(const S* __restrict__ src, int x, int y, int z, const PR<typename Codec<S>::R>& p,
+__device__ __forceinline__ void gather_impl(const S* __restrict__ src, int x, int y, int z, const PR<typename Codec<S>::R>& p,
                                        typename Codec<S>::R (&h)[Lat<D>::Q]) {
     using R = typename Codec<S>::R;
     const unsigned N = p.N;                  // Q * N < 2^32 is checked at create
@@ -246,21 +254,44 @@ __device__ __forceinline__ void gather(const S* __restrict__ src, int x, int y, 
         constexpr int i = decltype(I)::value;
         constexpr int a = Lat<D>::ex(i) + 1, b = Lat<D>::ey(i) + 1, c = Lat<D>::ez(i) + 1;
         constexpr R w = (R)weight<D>(i);
-        R d;
-        if (WALLS && (xo[a] || yo[b] || zo[c])) {
-            d = Codec<S>::ld(src + (Lat<D>::opp(i) * N + cell));
-            R wx = 0, wy = 0, wz = 0, cnt = 0;
-            // slot 2 (e = +1) crosses the lower wall (side 0), slot 0 (e = -1) the upper (side 1)
-            if (xo[a]) { constexpr int s = (a == 2) ? 0 : 1; wx += p.uw[0][s][0]; wy += p.uw[0][s][1]; wz += p.uw[0][s][2]; cnt += 1; }
-            if (yo[b]) { constexpr int s = (b == 2) ? 0 : 1; wx += p.uw[1][s][0]; wy += p.uw[1][s][1]; wz += p.uw[1][s][2]; cnt += 1; }
-            if (zo[c]) { constexpr int s = (c == 2) ? 0 : 1; wx += p.uw[2][s][0]; wy += p.uw[2][s][1]; wz += p.uw[2][s][2]; cnt += 1; }
-            const R eu = R(Lat<D>::ex(i)) * wx + R(Lat<D>::ey(i)) * wy + R(Lat<D>::ez(i)) * wz;
-            d += R(6) * eu / cnt;
+        if constexpr (WALLS) {
+            // branch-free: the address is selected and the load is unconditional, so the 27 loads
+            // issue back to back; the moving-wall term is added only where a wall was crossed
+            const bool bx = xo[a], by = yo[b], bz = zo[c];
+            const bool bounced = bx || by || bz;
+            const unsigned own = Lat<D>::opp(i) * N + cell;
+            const unsigned pulled = i * N + row[c][b] + (unsigned)xs[a];
+            R d = Codec<S>::ld(src + (bounced ? own : pulled));
+            constexpr int sx = (a == 2) ? 0 : 1, sy = (b == 2) ? 0 : 1, sz = (c == 2) ? 0 : 1;
+            R eu = R(0);
+            if constexpr (a != 1) eu += bx ? (R(Lat<D>::ex(i)) * p.uw[0][sx][0] + R(Lat<D>::ey(i)) * p.uw[0][sx][1] + R(Lat<D>::ez(i)) * p.uw[0][sx][2]) : R(0);
+            if constexpr (b != 1) eu += by ? (R(Lat<D>::ex(i)) * p.uw[1][sy][0] + R(Lat<D>::ey(i)) * p.uw[1][sy][1] + R(Lat<D>::ez(i)) * p.uw[1][sy][2]) : R(0);
+            if constexpr (c != 1) eu += bz ? (R(Lat<D>::ex(i)) * p.uw[2][sz][0] + R(Lat<D>::ey(i)) * p.uw[2][sz][1] + R(Lat<D>::ez(i)) * p.uw[2][sz][2]) : R(0);
+            const int cnt = (int)bx + (int)by + (int)bz;
+            const R inv_cnt = cnt >= 3 ? R(1) / 3 : cnt == 2 ? R(0.5) : R(1);
+            d += R(6) * eu * inv_cnt;
+            h[slot<D>(i)] = d * w;
         } else {
-            d = Codec<S>::ld(src + (i * N + row[c][b] + (unsigned)xs[a]));
+            h[slot<D>(i)] = Codec<S>::ld(src + (i * N + row[c][b] + (unsigned)xs[a])) * w;
         }
-        h[slot<D>(i)] = d * w;
     });
+}
+
+// Pull for a cell: the wall-aware version only where a link can cross a wall (cells in the first
+// or last layer of a bounce-back axis); everywhere else the periodic pull, which never leaves the
+// box on a wall axis there. With x-rows per warp, y and z are warp-uniform, so the branch only
+// diverges on x walls.
+template <int D, class S, bool WALLS>
+__device__ __forceinline__ void gather(const S* __restrict__ src, int x, int y, int z, const PR<typename Codec<S>::R>& p,
+                                       typename Codec<S>::R (&h)[Lat<D>::Q]) {
+    if constexpr (WALLS) {
+        const bool near = (p.bc[0] && (x == 0 || x == p.nx - 1)) || (p.bc[1] && (y == 0 || y == p.ny - 1)) ||
+                          (D == 3 && p.bc[2] && (z == 0 || z == p.nz - 1));
+        if (near) gather_impl<D, S, true>(src, x, y, z, p, h);
+        else gather_impl<D, S, false>(src, x, y, z, p, h);
+    } else {
+        gather_impl<D, S, false>(src, x, y, z, p, h);
+    }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -431,7 +462,7 @@ __device__ __forceinline__ void collide(R (&m)[Lat<D>::Q], const R F[3], const P
                 if constexpr (even) DM = fma(drho, tp, -excess<R, a == 2, b == 2, c == 2>(q));
                 else DM = -kw;
                 if (factorized) {
-                    // Sec. 11: products of relaxed second-order moments / rho^(k-1)
+                    // Sec. 13: products of relaxed second-order moments / rho^(k-1)
                     constexpr int ones = (a == 1) + (b == 1) + (c == 1);
                     if constexpr (ones == 0) {
                         const R pt[3] = {Txx * irho, Tyy * irho, Tzz * irho};

@@ -27,4 +27,16 @@ cudaError_t launch_adjoint_step(const void* state, const void* Ff, const Params&
                                 double* dLdF, cudaStream_t st);
 
 constexpr int kReduceMaxBlocks = 1216;
+
+// turbulence as forcing (turbulence.cu): scratch holds 10 N arithmetic values
+template <int D, class S>
+cudaError_t launch_turbulence_force(const void* state, void* force, const Params& p, double cs, void* scratch,
+                                    cudaStream_t st);
+
+// TMA-staged D3Q27 step (step_tma.cu)
+int tma_row_width(const Params& p, int esize);
+bool encode_tma_maps(const void* base, const Params& p, int storage, void* map_main, void* map_halo);
+template <class S>
+cudaError_t launch_step_tma(const void* map_main, const void* map_halo, const void* src, void* dst, const void* Ff,
+                            const Params& p, int* err, int nsm, cudaStream_t st);
 }  // namespace cm

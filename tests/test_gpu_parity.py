@@ -71,6 +71,12 @@ CASES = {
                          kw=dict(tau=0.8, omega_3=8.0 / 9.0, bc=("periodic", "bounceback", "periodic"),
                                  wall_velocity=[[[0, 0, 0], [0, 0, 0]], [[0.05, 0, 0], [0.05, 0, 0]], [[0, 0, 0], [0, 0, 0]]])),
     "d2q9_les_tgv": dict(lattice="D2Q9", shape=(1, 33, 31), flow="tgv", kw=dict(tau=0.55, smagorinsky_cs=0.2)),
+    "factorized": dict(lattice="D3Q27", shape=(6, 5, 40), flow="tgv",
+                       kw=dict(tau=0.58, omega_3=1.1, omega_4=1.3, attractor="factorized")),
+    "reduced": dict(lattice="D3Q27", shape=(5, 8, 33), flow="channel",
+                    kw=dict(tau=0.6, reduced_compressibility=True, rho0=1.0, bc=("periodic", "bounceback", "periodic"))),
+    "d2q9_factorized_reduced": dict(lattice="D2Q9", shape=(1, 17, 36), flow="tgv",
+                                    kw=dict(tau=0.7, attractor="factorized", reduced_compressibility=True, rho0=1.01)),
 }
 
 
@@ -319,3 +325,58 @@ def test_invalid_arguments_return_errors(cm):
             b.step_adjoint(b.new_state(), lam, torch.zeros_like(lam), torch.zeros(3, 64, dtype=torch.float64, device="cuda"))
         assert e.value.code == cm.ERR_UNSUPPORTED
         b.close()
+
+
+# D3Q27 cases the TMA-staged kernel takes (nx a multiple of 128)
+TMA_CASES = {
+    "tma_periodic_field": dict(lattice="D3Q27", shape=(5, 7, 256), flow="tgv", kw=dict(tau=0.6, omega_bulk=1.0)),
+    "tma_walls_les_vd": dict(lattice="D3Q27", shape=(6, 9, 128), flow="channel",
+                             kw=dict(tau=0.52, smagorinsky_cs=0.15, van_driest=(26.0, 8.0),
+                                     bc=("periodic", "bounceback", "bounceback"),
+                                     wall_velocity=[[[0, 0, 0], [0, 0, 0]], [[0.02, 0, 0.01], [-0.03, 0.0, 0.0]],
+                                                    [[0.01, 0, 0], [0, 0.02, 0]]])),
+    "tma_x_walls": dict(lattice="D3Q27", shape=(4, 5, 128), flow="tgv",
+                        kw=dict(tau=0.7, bc=("bounceback", "periodic", "periodic"),
+                                wall_velocity=[[[0, 0.01, 0], [0, 0, -0.02]], [[0, 0, 0], [0, 0, 0]], [[0, 0, 0], [0, 0, 0]]])),
+}
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("name", list(TMA_CASES))
+def test_tma_kernel_one_step_elementwise(cm, name, storage):
+    case = TMA_CASES[name]
+    rho, u, F = _inputs(case)
+    s, o = _pair(cm, case["lattice"], case["shape"], storage, rho, u, F, kernel="tma", **case["kw"])
+    s0 = s.get_state()
+    o.set_state(H.decode(s0, case["lattice"]))
+    s.step(1)
+    o.step(1)
+    got = H.decode(s.get_state(), case["lattice"])
+    w = H.lattice(case["lattice"]).w.view(-1, 1, 1, 1)
+    d_got, d_ref = got / w - 1, o.s / w - 1
+    tol = ONE_STEP_ATOL[storage] + ONE_STEP_RTOL[storage] * d_ref.abs()
+    err = (d_got - d_ref).abs()
+    assert bool((err <= tol).all()), f"max |dd| = {err.max().item():.3e}"
+    assert s.reduce()[0] > 0      # also checks the pipeline error flag
+    s.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_tma_and_direct_kernels_agree(cm, storage):
+    case = TMA_CASES["tma_walls_les_vd"]
+    rho, u, F = _inputs(case)
+    states = []
+    for kernel in ("tma", "direct"):
+        s, _ = _pair(cm, case["lattice"], case["shape"], storage, rho, u, F, kernel=kernel, **case["kw"])
+        s.step(15)
+        states.append(H.decode(s.get_state(), case["lattice"]))
+        s.close()
+    w = H.lattice(case["lattice"]).w.view(-1, 1, 1, 1)
+    diff = ((states[0] - states[1]) / w).abs().max().item()
+    assert diff < (1e-5 if storage == "f32" else 2e-2)
+
+
+def test_tma_requested_on_ineligible_config_is_rejected(cm):
+    with pytest.raises(cm.CmlbmError) as e:
+        cm.Solver(lattice="D3Q27", nx=150, ny=4, nz=4, storage="f32", kernel="tma")
+    assert e.value.code == cm.ERR_UNSUPPORTED

@@ -1,4 +1,4 @@
-"""Oracle pins: velocity set, orthogonal basis, exact inverse, equilibrium (Secs. 2, 4, 6, 8)."""
+"""Oracle pins: velocity set, orthogonal basis, exact inverse, equilibrium (Secs. 2, 4, 7, 9)."""
 import os
 
 import pytest
@@ -136,7 +136,7 @@ def test_d2q9_central_from_raw_printed_closed_forms():
                           - Fy * ux * uy + 2 * rho * ux * uy ** 2, atol=tol)
     assert torch.allclose(k[6], kxxy_r - 2 * ux * kxy_r - uy * kxx_r - 0.5 * Fy * ux ** 2
                           - Fx * ux * uy + 2 * rho * ux ** 2 * uy, atol=tol)
-    # conserved moments of fbar (Sec. 7): kbar_0 = rho, kbar_x = -F_x/2
+    # conserved moments of fbar (Sec. 8): kbar_0 = rho, kbar_x = -F_x/2
     assert torch.allclose(k[1], -0.5 * Fx, atol=1e-16)
     assert torch.allclose(k[2], -0.5 * Fy, atol=1e-16)
 

@@ -1,6 +1,6 @@
 """Oracle pins: source hierarchy, source populations, conservation, relaxation, literal form.
 
-Secs. 5-10 of the paper. Each pin compares the generic oracle against a route the paper
+Secs. 5-11 of the paper. Each pin compares the generic oracle against a route the paper
 prints independently (explicit formulas, velocity-space sources, element-wise update) or
 against an exact invariant.
 """
@@ -63,7 +63,7 @@ def test_source_populations_satisfy_exact_identity(name):
                 lo[d] -= 1
                 ref = ref + a[d] * F[d] / rho * kap[idx[tuple(lo)]]
         assert torch.allclose(sig[idx[a]], ref, atol=1e-15, rtol=1e-12), a
-    # conserved moments of f: kappa_0 = rho, kappa_x = 0 (Sec. 7)
+    # conserved moments of f: kappa_0 = rho, kappa_x = 0 (Sec. 8)
     for d in range(lat.d):
         e = [0, 0, 0]
         e[d] = 1
@@ -204,3 +204,60 @@ def test_literal_collision_kernel_raw_moments():
     ref = [z, z, z, 6 * g3 + 2 * g4, 6 * g3 - 2 * g4, 4 * g5, -4 * g6, -4 * g7, 8 * g3 + 4 * g8]
     for j in range(9):
         assert torch.allclose(r[j], ref[j], atol=1e-16, rtol=1e-12), j
+
+
+def _unit_state(lat, n, seed):
+    fb, F = _state(lat, n, seed)
+    return fb / fb.sum(0), F
+
+
+def test_reduced_compressibility_literal_equals_generic_without_force():
+    """Eqs. collisionkernelcompact3-8 (Sec. 12) equal the generic step with u = (sum fbar e + F/2)/rho0."""
+    lat = L.D2Q9
+    fb, F = _state(lat, 128, 21)
+    F = torch.zeros_like(F)
+    om = (1 / 0.7, 1 / 0.7, 1 / 0.7, 1.3, 1.3, 0.9)
+    for rho0 in (1.0, 1.02):
+        post_l, _, _ = LIT.collide_literal(fb, F, om, rho0=rho0)
+        p = C.Params(tau=0.7, omega3=1.3, omega4=0.9, reduced_compressibility=True, rho0=rho0)
+        post_g = C.collide(fb, F, lat, p)
+        assert (post_l - post_g).abs().max().item() < 1e-15
+
+
+def test_reduced_compressibility_equals_standard_at_reference_density():
+    lat = L.D3Q27
+    fb, F = _unit_state(lat, 32, 22)
+    p0 = C.Params(tau=0.62, omega3=1.2, omega4=0.8)
+    p1 = C.Params(tau=0.62, omega3=1.2, omega4=0.8, reduced_compressibility=True, rho0=1.0)
+    assert (C.collide(fb, F, lat, p0) - C.collide(fb, F, lat, p1)).abs().max().item() < 1e-15
+
+
+def test_factorized_literal_equals_generic_at_unit_density_without_force():
+    """Eq. factorxxyyfinal (Sec. 13) as printed equals the generic factorized attractor at rho = 1
+    (the reading divides the product by rho, which the paper writes for unit density)."""
+    lat = L.D2Q9
+    fb, F = _unit_state(lat, 128, 23)
+    F = torch.zeros_like(F)
+    om = (1 / 0.7, 1 / 0.7, 1 / 0.7, 1.3, 1.3, 0.9)
+    post_l, _, _ = LIT.collide_literal(fb, F, om, factorized=True)
+    post_g = C.collide(fb, F, lat, C.Params(tau=0.7, omega3=1.3, omega4=0.9, attractor="factorized"))
+    assert (post_l - post_g).abs().max().item() < 1e-15
+    # and it is a different collision from the Maxwellian attractor away from equilibrium
+    post_m = C.collide(fb, F, lat, C.Params(tau=0.7, omega3=1.3, omega4=0.9))
+    assert (post_g - post_m).abs().max().item() > 1e-4
+
+
+@pytest.mark.parametrize("name", ["D2Q9", "D3Q27"])
+def test_factorized_attractor_keeps_the_maxwellian_fixed_point(name):
+    """At equilibrium the relaxed second-order moments are Maxwellian and the products reduce to
+    rho c_s^(a+b+c): the factorized step leaves f^M unchanged (F = 0)."""
+    lat = L.get(name)
+    g = torch.Generator().manual_seed(24)
+    rho = 1 + 0.05 * torch.randn(32, generator=g, dtype=DT)
+    u = 0.1 * torch.randn(3, 32, generator=g, dtype=DT)
+    if lat.d == 2:
+        u[2] = 0
+    F = torch.zeros(3, 32, dtype=DT)
+    feq = C.equilibrium(rho, u, F, lat)
+    post = C.collide(feq, F, lat, C.Params(tau=0.7, omega3=1.2, omega4=0.9, attractor="factorized"))
+    assert (post - feq).abs().max().item() < 1e-15

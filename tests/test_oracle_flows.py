@@ -2,7 +2,7 @@
 
 * body-force Poiseuille: steady parabola u = F eta (H - eta) / (2 rho nu), exact with
   half-way walls when (1/omega_nu - 1/2)(1/omega_3 - 1/2) = 3/16 (nu = c_s^2 (1/omega_nu - 1/2),
-  Sec. 9), and the same profile shifted by U with walls and fluid moving at U (Galilean
+  Sec. 10), and the same profile shifted by U with walls and fluid moving at U (Galilean
   invariance of the forced flow, the paper's central claim);
 * Couette flow: exact linear profile (moving-wall bounce-back);
 * 2D Taylor-Green decay rate gives nu = c_s^2 (1/omega_nu - 1/2);
