@@ -218,6 +218,28 @@ CMLBM_API int cmlbm_step_adjoint(cmlbm_t* h, const void* state, const void* lamb
 /* Kernel launches issued by the handle so far (for benchmark accounting). */
 CMLBM_API long long cmlbm_launch_count(const cmlbm_t* h);
 
+/* ---- allocation-free reduction (no counterpart in the paper) --------------------------- *
+ * The FP64 reductions of cmlbm_reduce for callers that cannot allocate device memory: code
+ * recorded into a CUDA graph under capture, hosts whose device memory is owned by another
+ * allocator, or tools that must not create a handle (cmlbm_create allocates two state buffers).
+ * No handle and no allocation: the caller passes the configuration, a state buffer in the
+ * library's layout and storage format (device, Q*N elements), the force (uniform[3] added
+ * everywhere, NULL = 0; force_field = device [3][N] array in the arithmetic type -- double for
+ * CMLBM_F64 storage, float otherwise -- or NULL), and out, a device array of 5 doubles that
+ * receives {sum rho, sum rho u_x, sum rho u_y, sum rho u_z, sum rho |u|^2 / 2}.
+ * Launches asynchronously on cfg->stream (device cfg->device); the caller synchronises.
+ * Scratch: the per-block partial sums live in one file-scope device array of 16384 x 5
+ * doubles (640 KiB on every GPU that loads the library, kept until the process exits), so
+ * grids are limited to nx*ny*nz <= 16,777,216 cells; larger grids return CMLBM_ERR_INVALID
+ * before anything is launched. Every block overwrites its own partials, so nothing needs
+ * clearing between calls, but all calls share the array: calls that overlap on the GPU
+ * (different streams, or host threads racing) corrupt each other's sums. The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture begins.
+ * Errors: CMLBM_ERR_INVALID (NULL arguments, bad configuration, grid over the limit),
+ * CMLBM_ERR_CUDA (symbol lookup or launch failure). */
+CMLBM_API int cmlbm_reduce_noalloc(const cmlbm_config* cfg, const void* state, const double uniform_force[3],
+                                   const void* force_field, double* out);
 
 #ifdef __cplusplus
 }

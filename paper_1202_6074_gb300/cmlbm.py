@@ -28,7 +28,7 @@ BCS = {"periodic": PERIODIC, "bounceback": BOUNCEBACK}
 SYMBOLS = ["cmlbm_config_default", "cmlbm_create", "cmlbm_destroy", "cmlbm_last_error", "cmlbm_set_stream",
            "cmlbm_set_force", "cmlbm_init", "cmlbm_step", "cmlbm_step_buffers", "cmlbm_moments",
            "cmlbm_moments_of", "cmlbm_reduce", "cmlbm_state_bytes", "cmlbm_get_state", "cmlbm_set_state",
-           "cmlbm_adjoint_terminal", "cmlbm_step_adjoint", "cmlbm_launch_count",
+           "cmlbm_adjoint_terminal", "cmlbm_step_adjoint", "cmlbm_launch_count", "cmlbm_reduce_noalloc",
            "cmlbm_turbulence_force", "cmlbm_step_filtered"]
 
 
@@ -92,6 +92,7 @@ def load():
         "cmlbm_adjoint_terminal": (I, [P, P, P, P, P, P]),
         "cmlbm_step_adjoint": (I, [P, P, P, P, P]),
         "cmlbm_launch_count": (ctypes.c_longlong, [P]),
+        "cmlbm_reduce_noalloc": (I, [ctypes.POINTER(Config), P, D, P, P]),
         "cmlbm_turbulence_force": (I, [P, ctypes.c_double]),
         "cmlbm_step_filtered": (I, [P, I, ctypes.c_double]),
     }
@@ -282,6 +283,16 @@ class Solver:
 
     def step_adjoint(self, state, lam_in, lam_out, dLdF):
         self._check(self.lib.cmlbm_step_adjoint(self.h, _ptr(state), _ptr(lam_in), _ptr(lam_out), _ptr(dLdF)))
+
+
+def reduce_noalloc(cfg, state, out, uniform_force=(0.0, 0.0, 0.0), force_field=None):
+    """cmlbm_reduce_noalloc: FP64 sums of a state buffer into the device tensor out[5] without
+    a handle or any allocation (the call is asynchronous on cfg.stream)."""
+    lib = load()
+    rc = lib.cmlbm_reduce_noalloc(ctypes.byref(cfg), _ptr(state), _as_vec3(uniform_force), _ptr(force_field),
+                                  _ptr(out))
+    if rc != OK:
+        raise CmlbmError(rc, "cmlbm_reduce_noalloc rejected the call (see include/cmlbm.h)")
 
 
 def rest_weights(lattice):
