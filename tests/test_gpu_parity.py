@@ -380,3 +380,37 @@ def test_tma_requested_on_ineligible_config_is_rejected(cm):
     with pytest.raises(cm.CmlbmError) as e:
         cm.Solver(lattice="D3Q27", nx=150, ny=4, nz=4, storage="f32", kernel="tma")
     assert e.value.code == cm.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("lattice,storage,tol", [("D3Q27", "f64", 1e-12), ("D3Q27", "f32", 2e-5), ("D2Q9", "f64", 1e-12)])
+def test_filtered_step_matches_oracle(cm, lattice, storage, tol):
+    """Turbulence as forcing (Sec. 14): Smagorinsky closure force + factorized, reduced step."""
+    shape = (6, 10, 12) if lattice == "D3Q27" else (1, 14, 18)
+    nz, ny, nx = shape
+    rho, u = W.random_solenoidal(nx, ny, nz, seed=7, u_rms=0.04)
+    if lattice == "D2Q9":
+        u[2] = 0
+    kw = dict(tau=0.55, attractor="factorized", reduced_compressibility=True, rho0=1.0)
+    s, o = _pair(cm, lattice, shape, storage, rho, u, None, uniform=(2e-6, 0.0, 0.0), **kw)
+    s.step_filtered(5, 0.18)
+    o.step_filtered(5, 0.18)
+    rg, ug = s.moments()
+    ro, uo = o.moments()
+    assert H.rel_l2(ug, uo) < tol
+    s.close()
+    # with C_s = 0 the closure force is exactly the uniform force: same state as a plain step
+    a, _ = _pair(cm, lattice, shape, storage, rho, u, None, uniform=(2e-6, 0.0, 0.0), **kw)
+    b, _ = _pair(cm, lattice, shape, storage, rho, u, None, uniform=(2e-6, 0.0, 0.0), **kw)
+    a.step_filtered(3, 0.0)
+    b.step(3)
+    assert torch.equal(a.get_state(), b.get_state())
+    a.close()
+    b.close()
+
+
+def test_filtered_step_rejects_walls(cm):
+    s = cm.Solver(lattice="D3Q27", nx=8, ny=8, nz=8, storage="f32", bc=("periodic", "bounceback", "periodic"))
+    with pytest.raises(cm.CmlbmError) as e:
+        s.turbulence_force(0.1)
+    assert e.value.code == cm.ERR_UNSUPPORTED
+    s.close()
