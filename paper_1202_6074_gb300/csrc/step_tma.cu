@@ -79,7 +79,9 @@ template <class S, int TX, int STAGES> __host__ __device__ constexpr size_t tma_
     return (size_t)STAGES * stage_bytes<S, TX>() + 2 * STAGES * sizeof(uint64_t) + 128;   // +128: base alignment
 }
 
-template <class S, int TX, int STAGES, class FT>
+// HALO = false: the tile spans the whole periodic row (TX == nx), so the x-neighbours of the
+// first and last cells are the other end of the same staged row and no halo copies are issued.
+template <class S, int TX, int STAGES, class FT, bool HALO>
 __global__ void __launch_bounds__(TX + 32, 2) k_step_tma(const __grid_constant__ CUtensorMap map_main,
                                                         const __grid_constant__ CUtensorMap map_halo,
                                                         const S* __restrict__ src, S* __restrict__ dst,
@@ -91,7 +93,7 @@ __global__ void __launch_bounds__(TX + 32, 2) k_step_tma(const __grid_constant__
     constexpr uint32_t kStageBytes = stage_bytes<S, TX>();
     constexpr uint32_t kMainBytes = (uint32_t)(TX * sizeof(S));
     static_assert(kMainBytes % 128 == 0, "main rows must keep 128-byte alignment");
-    constexpr uint32_t kTxBytes = (uint32_t)(Q * (TX * sizeof(S) + 2 * 16));
+    constexpr uint32_t kTxBytes = (uint32_t)(Q * (TX * sizeof(S) + (HALO ? 2 * 16 : 0)));
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // 128-byte aligned base inside the dynamic shared memory (the allocation has 128 B of slack)
     const uint32_t raw = smem_addr(smem_raw);
@@ -106,7 +108,17 @@ __global__ void __launch_bounds__(TX + 32, 2) k_step_tma(const __grid_constant__
 
     const int tid = threadIdx.x;
     const int nxt = p.nx / TX;
-    const long long nrows = (long long)nxt * p.ny * p.nz;
+    const int nrows = nxt * p.ny * p.nz;           // < 2^31 (cells < 2^31)
+    // rows are visited r = blockIdx.x, blockIdx.x + gridDim.x, ...; (xt, y, z) advance with carries
+    const int g = (int)gridDim.x;
+    const int gx = g % nxt, gy = (g / nxt) % p.ny, gz = g / (nxt * p.ny);
+    const int b0 = (int)blockIdx.x;
+    const int x00 = b0 % nxt, y00 = (b0 / nxt) % p.ny, z00 = b0 / (nxt * p.ny);
+    auto advance = [&](int& xt, int& y, int& z) {
+        xt += gx; y += gy; z += gz;
+        if (xt >= nxt) { xt -= nxt; ++y; }
+        if (y >= p.ny) { y -= p.ny; ++z; }
+    };
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
@@ -120,7 +132,8 @@ __global__ void __launch_bounds__(TX + 32, 2) k_step_tma(const __grid_constant__
         // ---------------- producer warp: lane i issues direction i's three copies ----------------
         const int lane = tid - TX;
         int k = 0;
-        for (long long r = blockIdx.x; r < nrows; r += gridDim.x, ++k) {
+        int xt = x00, y = y00, z = z00;
+        for (int r = b0; r < nrows; r += g, ++k, advance(xt, y, z)) {
             const int s = k % STAGES;
             const uint32_t ph = (uint32_t)(k / STAGES) & 1u;
             bool ok = true;
@@ -135,9 +148,6 @@ __global__ void __launch_bounds__(TX + 32, 2) k_step_tma(const __grid_constant__
                 }
                 return;
             }
-            const int xt = (int)(r % nxt);
-            const long long rest = r / nxt;
-            const int y = (int)(rest % p.ny), z = (int)(rest / p.ny);
             const int x0 = xt * TX;
             int xl = x0 - A, xr = x0 + TX;
             if (xl < 0) xl = (FT::WALLS && p.bc[0]) ? 0 : xl + p.nx;
@@ -152,9 +162,11 @@ __global__ void __launch_bounds__(TX + 32, 2) k_step_tma(const __grid_constant__
                 if (zs < 0) zs = (FT::WALLS && p.bc[2]) ? 0 : zs + p.nz;
                 else if (zs >= p.nz) zs = (FT::WALLS && p.bc[2]) ? p.nz - 1 : zs - p.nz;
                 tma_load_4d(main_row(s, i), &map_main, &full[s], x0, ys, zs, i);
-                const S* grow = src + ((size_t)i * p.N + ((size_t)zs * p.ny + ys) * p.nx);
-                bulk_load(halo_row(s, i, 0), grow + xl, 16, &full[s]);
-                bulk_load(halo_row(s, i, 1), grow + xr, 16, &full[s]);
+                if constexpr (HALO) {
+                    const S* grow = src + ((size_t)i * p.N + ((size_t)zs * p.ny + ys) * p.nx);
+                    bulk_load(halo_row(s, i, 0), grow + xl, 16, &full[s]);
+                    bulk_load(halo_row(s, i, 1), grow + xr, 16, &full[s]);
+                }
             }
         }
         return;
@@ -164,16 +176,14 @@ __global__ void __launch_bounds__(TX + 32, 2) k_step_tma(const __grid_constant__
     const unsigned N = p.N;
     const int lane = tid & 31;
     int k = 0;
-    for (long long r = blockIdx.x; r < nrows; r += gridDim.x, ++k) {
+    int xt = x00, y = y00, z = z00;
+    for (int r = b0; r < nrows; r += g, ++k, advance(xt, y, z)) {
         const int s = k % STAGES;
         const uint32_t ph = (uint32_t)(k / STAGES) & 1u;
         if (!mbar_wait(&full[s], ph)) {
             atomicExch(err, 2);
             return;
         }
-        const int xt = (int)(r % nxt);
-        const long long rest = r / nxt;
-        const int y = (int)(rest % p.ny), z = (int)(rest / p.ny);
         const int x = xt * TX + tid;
         const unsigned cell = (unsigned)((z * p.ny + y) * p.nx + x);
         const bool near = FT::WALLS && ((p.bc[0] && (x == 0 || x == p.nx - 1)) || (p.bc[1] && (y == 0 || y == p.ny - 1)) ||
@@ -185,8 +195,13 @@ __global__ void __launch_bounds__(TX + 32, 2) k_step_tma(const __grid_constant__
             constexpr R w = (R)weight<3>(i);
             const int j = tid - ex;       // position in the staged row; -1 and TX are the halos
             const S* ptr = main_row(s, i) + j;
-            if constexpr (ex > 0) ptr = (j < 0) ? halo_row(s, i, 0) + (A - 1) : ptr;
-            if constexpr (ex < 0) ptr = (j >= TX) ? halo_row(s, i, 1) : ptr;
+            if constexpr (HALO) {
+                if constexpr (ex > 0) ptr = (j < 0) ? halo_row(s, i, 0) + (A - 1) : ptr;
+                if constexpr (ex < 0) ptr = (j >= TX) ? halo_row(s, i, 1) : ptr;
+            } else {          // whole periodic row: wrap inside the staged row
+                if constexpr (ex > 0) ptr = (j < 0) ? main_row(s, i) + (TX - 1) : ptr;
+                if constexpr (ex < 0) ptr = (j >= TX) ? main_row(s, i) : ptr;
+            }
             R d = Codec<S>::ld_shared(ptr);
             if constexpr (FT::WALLS) {
                 if (near) {
@@ -218,7 +233,7 @@ __global__ void __launch_bounds__(TX + 32, 2) k_step_tma(const __grid_constant__
     }
 }
 
-template <class S, int TX, int STAGES, class FT>
+template <class S, int TX, int STAGES, class FT, bool HALO>
 cudaError_t launch_tma_ft(const void* map_main, const void* map_halo, const void* src, void* dst, const void* Ff,
                           const Params& p, int* err, int nsm, cudaStream_t st) {
     using R = typename Codec<S>::R;
@@ -227,7 +242,7 @@ cudaError_t launch_tma_ft(const void* map_main, const void* map_halo, const void
     // 16-byte aligned (checked here, before anything is launched)
     if (((uintptr_t)src % 16) != 0 || ((size_t)p.nx * sizeof(S)) % 16 != 0 || (p.nx % TX) != 0)
         return cudaErrorMisalignedAddress;
-    auto kern = k_step_tma<S, TX, STAGES, FT>;
+    auto kern = k_step_tma<S, TX, STAGES, FT, HALO>;
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -240,6 +255,7 @@ cudaError_t launch_tma_ft(const void* map_main, const void* map_halo, const void
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const long long nrows = (long long)(p.nx / TX) * p.ny * p.nz;
     long long grid = (long long)per_sm * nsm;
+    if (!HALO && (p.nx != TX || p.bc[0])) return cudaErrorInvalidValue;
     if (grid > nrows) grid = nrows;
     kern<<<(unsigned)grid, TX + 32, smem, st>>>(*(const CUtensorMap*)map_main, *(const CUtensorMap*)map_halo,
                                                (const S*)src, (S*)dst, (const R*)Ff, typed<R>(p), err);
@@ -251,9 +267,11 @@ cudaError_t launch_tma_tx(const void* mm, const void* mh, const void* src, void*
                           int* err, int nsm, cudaStream_t st) {
     const bool w = p.bc[0] || p.bc[1] || p.bc[2];
     const bool l = p.les, f = p.has_field;
-#define CM_TMA_CASE(W_, L_, F_) \
-    if (w == W_ && l == L_ && f == F_) \
-        return launch_tma_ft<S, TX, STAGES, Feat<W_, L_, F_, false>>(mm, mh, src, dst, Ff, p, err, nsm, st);
+    const bool halo = !(p.nx == TX && !p.bc[0]);
+#define CM_TMA_CASE(W_, L_, F_)                                                                                        \
+    if (w == W_ && l == L_ && f == F_)                                                                                 \
+        return halo ? launch_tma_ft<S, TX, STAGES, Feat<W_, L_, F_, false>, true>(mm, mh, src, dst, Ff, p, err, nsm, st) \
+                    : launch_tma_ft<S, TX, STAGES, Feat<W_, L_, F_, false>, false>(mm, mh, src, dst, Ff, p, err, nsm, st);
     CM_TMA_CASE(false, false, false)
     CM_TMA_CASE(false, false, true)
     CM_TMA_CASE(false, true, false)
