@@ -62,7 +62,7 @@ extern "C" {
 /* ---- enumerations ------------------------------------------------------------------ */
 enum { CMLBM_D2Q9 = 0, CMLBM_D3Q27 = 1 };                          /* lattice */
 enum { CMLBM_F64 = 0, CMLBM_F32 = 1, CMLBM_BF16 = 2, CMLBM_F16 = 3 }; /* state storage */
-enum { CMLBM_PERIODIC = 0, CMLBM_BOUNCEBACK = 1 };                 /* per-axis boundary */
+enum { CMLBM_PERIODIC = 0, CMLBM_BOUNCEBACK = 1, CMLBM_HALO = 2 };  /* per-axis boundary */
 enum { CMLBM_DEVICE = 0, CMLBM_HOST = 1 };                         /* where a buffer lives */
 enum { CMLBM_ATTRACTOR_MAXWELL = 0, CMLBM_ATTRACTOR_FACTORIZED = 1 };
 enum { CMLBM_KERNEL_AUTO = 0, CMLBM_KERNEL_DIRECT = 1, CMLBM_KERNEL_TMA = 2 };
@@ -77,6 +77,9 @@ typedef struct cmlbm cmlbm_t;
  *                         first and last cells of that axis (paper silent on boundaries):
  *                         g_i(x) = s_ibar(x) + 2 w_i rho_w (e_i . u_w) / c_s^2, rho_w = 1, u_w the
  *                         crossed wall's velocity (the mean of both walls on an edge link).
+ *                         CMLBM_HALO (z axis of D3Q27 only): the handle is one z-slab of a larger
+ *                         domain (see "slab decomposition" below); each state buffer carries one
+ *                         ghost plane below z = 0 and one above z = nz - 1, and z does not wrap.
  *   wall_velocity[a][s]   velocity of the wall on axis a, side s (0 = below index 0, 1 = above n-1).
  *   tau                   shear relaxation time: omega_nu = 1/tau, nu = c_s^2 (tau - 1/2)
  *                         (Sec. 10, text after Eq. collisionkernelg8). Must satisfy tau > 1/2.
@@ -177,7 +180,8 @@ CMLBM_API int cmlbm_moments_of(cmlbm_t* h, const void* state, double* rho, doubl
  * step since the last check gave up on a bounded pipeline wait (its output is then invalid). */
 CMLBM_API int cmlbm_reduce(cmlbm_t* h, double out[5]);
 
-/* Bytes of one state buffer (Q * N * storage size). */
+/* Bytes of one state buffer: Q * N * storage size, or Q * nx * ny * (nz + 2) * storage size
+ * with bc[2] = CMLBM_HALO (the ghost planes are part of the state). */
 CMLBM_API size_t cmlbm_state_bytes(const cmlbm_t* h);
 
 /* Copy the current state out of / into the handle (raw storage format, bytes must equal
@@ -214,6 +218,41 @@ CMLBM_API int cmlbm_adjoint_terminal(cmlbm_t* h, const void* state, const double
 /* One step back: state is s_t (the input of the step s_t -> s_{t+1}), lambda_in = dL/ds_{t+1},
  * lambda_out = dL/ds_t (must not alias lambda_in); adds (dC/dF)^T lambda_in into dLdF. */
 CMLBM_API int cmlbm_step_adjoint(cmlbm_t* h, const void* state, const void* lambda_in, void* lambda_out, double* dLdF);
+
+/* ---- slab decomposition along z (no counterpart in the paper) -------------------------- *
+ * A periodic-in-z D3Q27 domain split into z-slabs, one handle per slab, each created with
+ * bc[2] = CMLBM_HALO and nz = its own number of planes. The streaming step (Eq.
+ * cascadedstreaming1) pulls s_i(x - e_i): the only values a slab reads from outside itself are
+ * those of the 9 directions with e_z = +1 from the plane just below it and of the 9 with
+ * e_z = -1 from the plane just above. Each state buffer is laid out [Q][nz + 2][ny][nx] with
+ * those two ghost planes at z = -1 and z = nz; steps, moments and reductions cover the nz own
+ * planes and read the ghosts. After every step the caller refreshes the ghosts from the
+ * neighbours (the slab below is the periodic predecessor, the slab above the successor):
+ *     top    = pack(CMLBM_FACE_TOP)     -> unpack(CMLBM_FACE_BOTTOM) on the slab above
+ *     bottom = pack(CMLBM_FACE_BOTTOM)  -> unpack(CMLBM_FACE_TOP)    on the slab below
+ * cmlbm_init writes valid ghosts itself (the inverse pull of the slab's own cells), so the first
+ * step needs no exchange. A one-slab domain is its own neighbour on both sides. Moving and
+ * resting walls on x and y, force fields, eddy viscosity and all collision forms work as in a
+ * single domain; the TMA step, the adjoint and turbulence forcing return
+ * CMLBM_ERR_UNSUPPORTED on a slab handle. */
+enum { CMLBM_FACE_BOTTOM = 0, CMLBM_FACE_TOP = 1 };
+
+/* Bytes of one face message: 9 * nx * ny values in the storage format. */
+CMLBM_API size_t cmlbm_halo_bytes(const cmlbm_t* h);
+
+/* Copy the 9 populations that leave the slab through `face` out of the current state:
+ * CMLBM_FACE_TOP = directions with e_z = +1 of plane nz - 1, CMLBM_FACE_BOTTOM = e_z = -1 of
+ * plane 0. out holds [9][ny][nx] values in the storage format, directions in increasing
+ * lexicographic order (index 9 (e_z + 1) + 3 (e_y + 1) + (e_x + 1)); where = CMLBM_DEVICE
+ * (asynchronous on the handle's stream) or CMLBM_HOST (returns when the copy has landed).
+ * CMLBM_ERR_INVALID for a bad face, NULL out, or a handle without CMLBM_HALO on z. */
+CMLBM_API int cmlbm_halo_pack(cmlbm_t* h, int face, void* out, int where);
+
+/* Write a neighbour's face message into a ghost plane of the current state:
+ * CMLBM_FACE_BOTTOM = the ghost below (takes the slab below's TOP message), CMLBM_FACE_TOP =
+ * the ghost above (takes the slab above's BOTTOM message). Layout and `where` as for
+ * cmlbm_halo_pack; a host buffer may be reused when the call returns. */
+CMLBM_API int cmlbm_halo_unpack(cmlbm_t* h, int face, const void* in, int where);
 
 /* Kernel launches issued by the handle so far (for benchmark accounting). */
 CMLBM_API long long cmlbm_launch_count(const cmlbm_t* h);

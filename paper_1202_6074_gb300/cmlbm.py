@@ -16,20 +16,22 @@ LIB_PATH = os.path.join(HERE, "libcmlbm.so")
 OK, ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_UNSUPPORTED, ERR_DIVERGED = 0, -1, -2, -3, -4, -5
 D2Q9, D3Q27 = 0, 1
 F64, F32, BF16, F16 = 0, 1, 2, 3
-PERIODIC, BOUNCEBACK = 0, 1
+PERIODIC, BOUNCEBACK, HALO = 0, 1, 2
 DEVICE, HOST = 0, 1
+FACE_BOTTOM, FACE_TOP = 0, 1
 
 LATTICES = {"D2Q9": D2Q9, "D3Q27": D3Q27}
 STORAGES = {"f64": F64, "f32": F32, "bf16": BF16, "f16": F16}
 TORCH_STORAGE = {F64: torch.float64, F32: torch.float32, BF16: torch.bfloat16, F16: torch.float16}
-BCS = {"periodic": PERIODIC, "bounceback": BOUNCEBACK}
+BCS = {"periodic": PERIODIC, "bounceback": BOUNCEBACK, "halo": HALO}
 
 # every symbol declared in include/cmlbm.h
 SYMBOLS = ["cmlbm_config_default", "cmlbm_create", "cmlbm_destroy", "cmlbm_last_error", "cmlbm_set_stream",
            "cmlbm_set_force", "cmlbm_init", "cmlbm_step", "cmlbm_step_buffers", "cmlbm_moments",
            "cmlbm_moments_of", "cmlbm_reduce", "cmlbm_state_bytes", "cmlbm_get_state", "cmlbm_set_state",
            "cmlbm_adjoint_terminal", "cmlbm_step_adjoint", "cmlbm_launch_count", "cmlbm_reduce_noalloc",
-           "cmlbm_turbulence_force", "cmlbm_step_filtered"]
+           "cmlbm_turbulence_force", "cmlbm_step_filtered", "cmlbm_halo_bytes", "cmlbm_halo_pack",
+           "cmlbm_halo_unpack"]
 
 
 class Config(ctypes.Structure):
@@ -95,6 +97,9 @@ def load():
         "cmlbm_reduce_noalloc": (I, [ctypes.POINTER(Config), P, D, P, P]),
         "cmlbm_turbulence_force": (I, [P, ctypes.c_double]),
         "cmlbm_step_filtered": (I, [P, I, ctypes.c_double]),
+        "cmlbm_halo_bytes": (ctypes.c_size_t, [P]),
+        "cmlbm_halo_pack": (I, [P, I, P, I]),
+        "cmlbm_halo_unpack": (I, [P, I, P, I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -175,6 +180,9 @@ class Solver:
         self.Q = 27 if self.cfg.lattice == D3Q27 else 9
         self.shape = (self.cfg.nz, self.cfg.ny, self.cfg.nx)
         self.N = self.cfg.nx * self.cfg.ny * self.cfg.nz
+        self.slab = self.cfg.bc[2] == HALO
+        # a slab's state buffers carry a ghost plane below and above its own planes
+        self.state_shape = (self.Q, self.cfg.nz + (2 if self.slab else 0), self.cfg.ny, self.cfg.nx)
         self.device = torch.device("cuda", self.cfg.device)
         self.state_dtype = TORCH_STORAGE[self.cfg.storage]
         self.real_dtype = torch.float64 if self.cfg.storage == F64 else torch.float32
@@ -262,7 +270,31 @@ class Solver:
         return int(self.lib.cmlbm_state_bytes(self.h))
 
     def new_state(self):
-        return torch.empty((self.Q,) + self.shape, dtype=self.state_dtype, device=self.device)
+        return torch.empty(self.state_shape, dtype=self.state_dtype, device=self.device)
+
+    # ---- slab faces -------------------------------------------------------------------
+    def new_face(self, host=False):
+        """A face message buffer [9, ny, nx] in the storage type (pinned host memory if host)."""
+        shape = (9, self.cfg.ny, self.cfg.nx)
+        if host:
+            return torch.empty(shape, dtype=self.state_dtype, pin_memory=torch.cuda.is_available())
+        return torch.empty(shape, dtype=self.state_dtype, device=self.device)
+
+    def pack(self, face, out=None, host=False):
+        """The 9 populations leaving through `face` (FACE_TOP: e_z = +1, FACE_BOTTOM: e_z = -1)."""
+        out = self.new_face(host) if out is None else out
+        self._check(self.lib.cmlbm_halo_pack(self.h, int(face), _ptr(out), HOST if out.device.type == "cpu" else DEVICE))
+        return out
+
+    def unpack(self, face, msg):
+        """Write a neighbour's message into the ghost plane on `face` of the current state."""
+        if msg.device.type != "cpu":
+            msg = msg.to(self.device, self.state_dtype).contiguous()
+        else:
+            msg = msg.to(self.state_dtype).contiguous()
+        self._check(self.lib.cmlbm_halo_unpack(self.h, int(face), _ptr(msg),
+                                               HOST if msg.device.type == "cpu" else DEVICE))
+        self._face_keepalive = msg
 
     def get_state(self, out=None):
         out = self.new_state() if out is None else out

@@ -34,6 +34,7 @@ struct cmlbm {
     int* flag = nullptr;       // device error flag of the bounded pipeline waits
     int nsm = 0;
     void* turb = nullptr;      // [10][N] arithmetic type: rho, u, eddy stress (turbulence forcing)
+    size_t ghost = 0;          // elements before the first own plane of a state buffer (nx ny on a slab)
 };
 
 namespace {
@@ -106,6 +107,10 @@ cudaError_t do_step_tma(cmlbm* h, const void* map_main, const void* map_halo, co
     return cudaErrorInvalidValue;
 }
 
+// the kernels address a state buffer from its first own plane (past the ghost plane of a slab)
+const void* own(const cmlbm* h, const void* b) { return (const char*)b + h->ghost * h->esize; }
+void* own(const cmlbm* h, void* b) { return (char*)b + h->ghost * h->esize; }
+
 cudaError_t do_step(cmlbm* h, const void* src, void* dst) {
     ++h->launches;
     if (h->tma) {
@@ -116,7 +121,7 @@ cudaError_t do_step(cmlbm* h, const void* src, void* dst) {
     }
     return dispatch(h, [&](auto d, auto* s) {
         using S = std::remove_pointer_t<decltype(s)>;
-        return cm::launch_step<decltype(d)::value, S>(src, dst, h->force, h->p, h->st);
+        return cm::launch_step<decltype(d)::value, S>(own(h, src), own(h, dst), h->force, h->p, h->st);
     });
 }
 
@@ -124,7 +129,7 @@ cudaError_t do_moments(cmlbm* h, const void* src, double* rho, double* u) {
     ++h->launches;
     return dispatch(h, [&](auto d, auto* s) {
         using S = std::remove_pointer_t<decltype(s)>;
-        return cm::launch_moments<decltype(d)::value, S>(src, h->force, h->p, rho, u, h->st);
+        return cm::launch_moments<decltype(d)::value, S>(own(h, src), h->force, h->p, rho, u, h->st);
     });
 }
 
@@ -176,8 +181,16 @@ int cmlbm_create(const cmlbm_config* cfg, cmlbm_t** out) {
     if (c.nz > 65535) return fail(nullptr, CMLBM_ERR_INVALID, "nz must be <= 65535");
     if (c.ny > 65535) return fail(nullptr, CMLBM_ERR_INVALID, "ny must be <= 65535");
     for (int a = 0; a < 3; ++a)
-        if (c.bc[a] != CMLBM_PERIODIC && c.bc[a] != CMLBM_BOUNCEBACK)
-            return fail(nullptr, CMLBM_ERR_INVALID, "bc must be CMLBM_PERIODIC or CMLBM_BOUNCEBACK");
+        if (c.bc[a] != CMLBM_PERIODIC && c.bc[a] != CMLBM_BOUNCEBACK && !(a == 2 && c.bc[a] == CMLBM_HALO))
+            return fail(nullptr, CMLBM_ERR_INVALID,
+                        "bc must be CMLBM_PERIODIC or CMLBM_BOUNCEBACK (or CMLBM_HALO on z)");
+    const bool slab = c.bc[2] == CMLBM_HALO;
+    if (slab && c.lattice != CMLBM_D3Q27) return fail(nullptr, CMLBM_ERR_INVALID, "CMLBM_HALO needs D3Q27");
+    const long long S = slab ? (long long)c.nx * c.ny * (c.nz + 2) : N;
+    if (S * (c.lattice == CMLBM_D3Q27 ? 27 : 9) >= (1LL << 32))
+        return fail(nullptr, CMLBM_ERR_INVALID, "Q*nx*ny*(nz+2) must be < 2^32 on a slab (32-bit element offsets)");
+    if (slab && c.kernel == CMLBM_KERNEL_TMA)
+        return fail(nullptr, CMLBM_ERR_UNSUPPORTED, "the TMA-staged step does not cover slab handles");
     if (!(c.tau > 0.5) || !std::isfinite(c.tau)) return fail(nullptr, CMLBM_ERR_INVALID, "tau must be > 1/2");
     if (c.omega_bulk != 0.0 && !valid_omega(c.omega_bulk)) return fail(nullptr, CMLBM_ERR_INVALID, "omega_bulk must be 0 or in (0, 2)");
     if (!valid_omega(c.omega_3) || !valid_omega(c.omega_4)) return fail(nullptr, CMLBM_ERR_INVALID, "omega_3 and omega_4 must be in (0, 2)");
@@ -206,6 +219,8 @@ int cmlbm_create(const cmlbm_config* cfg, cmlbm_t** out) {
     p.ny = c.ny;
     p.nz = c.nz;
     p.N = N;
+    p.S = S;
+    h->ghost = slab ? (size_t)c.nx * c.ny : 0;
     for (int a = 0; a < 3; ++a) p.bc[a] = c.bc[a];
     std::memcpy(p.uw, c.wall_velocity, sizeof(p.uw));
     p.tau0 = c.tau;
@@ -226,7 +241,7 @@ int cmlbm_create(const cmlbm_config* cfg, cmlbm_t** out) {
         delete h;
         return fail(nullptr, CMLBM_ERR_CUDA, "cudaSetDevice failed");
     }
-    const size_t bytes = (size_t)h->Q * (size_t)N * h->esize;
+    const size_t bytes = (size_t)h->Q * (size_t)S * h->esize;
     for (int k = 0; k < 2; ++k) {
         if (cudaMalloc(&h->buf[k], bytes) != cudaSuccess) {
             cudaGetLastError();
@@ -293,7 +308,7 @@ int cmlbm_set_stream(cmlbm_t* h, void* stream) {
 
 long long cmlbm_launch_count(const cmlbm_t* h) { return h ? h->launches : 0; }
 
-size_t cmlbm_state_bytes(const cmlbm_t* h) { return h ? (size_t)h->Q * (size_t)h->p.N * h->esize : 0; }
+size_t cmlbm_state_bytes(const cmlbm_t* h) { return h ? (size_t)h->Q * (size_t)h->p.S * h->esize : 0; }
 
 int cmlbm_set_force(cmlbm_t* h, const double uniform[3], const double* field, int where) {
     if (!h) return CMLBM_ERR_INVALID;
@@ -356,8 +371,8 @@ int cmlbm_init(cmlbm_t* h, const double* rho, const double* u, int where) {
             du = h->stage + N;
         }
     }
-    void* tmp = h->buf[1 - h->cur];
-    void* dst = h->buf[h->cur];
+    void* tmp = own(h, h->buf[1 - h->cur]);
+    void* dst = own(h, h->buf[h->cur]);
     h->launches += 2;
     cudaError_t e = dispatch(h, [&](auto d, auto* s) {
         using S = std::remove_pointer_t<decltype(s)>;
@@ -428,7 +443,7 @@ int cmlbm_reduce(cmlbm_t* h, double out[5]) {
     h->launches += 2;
     cudaError_t e = dispatch(h, [&](auto d, auto* s) {
         using S = std::remove_pointer_t<decltype(s)>;
-        return cm::launch_reduce<decltype(d)::value, S>(h->buf[h->cur], h->force, h->p, h->part, h->red, h->st);
+        return cm::launch_reduce<decltype(d)::value, S>(own(h, h->buf[h->cur]), h->force, h->p, h->part, h->red, h->st);
     });
     if (e != cudaSuccess) return cuda_fail(h, e, "reduction kernels");
     e = cudaMemcpyAsync(out, h->red, sizeof(double) * 5, cudaMemcpyDeviceToHost, h->st);
@@ -513,6 +528,7 @@ int cmlbm_step_filtered(cmlbm_t* h, int nsteps, double cs) {
 }
 
 static int adjoint_supported(cmlbm* h) {
+    if (h->ghost) return fail(h, CMLBM_ERR_UNSUPPORTED, "the adjoint does not cover slab handles");
     if (h->cfg.storage != CMLBM_F64 && h->cfg.storage != CMLBM_F32)
         return fail(h, CMLBM_ERR_UNSUPPORTED, "the adjoint needs F64 or F32 storage");
     if (h->p.les || h->p.attractor != 0 || h->p.reduced)
@@ -560,6 +576,51 @@ int cmlbm_step_adjoint(cmlbm_t* h, const void* state, const void* lambda_in, voi
                 : cm::launch_adjoint_step<2, float>(state, h->force, h->p, lambda_in, lambda_out, dLdF, h->st);
     if (e != cudaSuccess) return cuda_fail(h, e, "adjoint step kernel");
     return CMLBM_OK;
+}
+
+// ---- slab decomposition: face messages ----------------------------------------------------
+// A face message is 9 direction planes of one z-plane: directions 9 (e_z + 1) + 0..8, i.e.
+// 0..8 (e_z = -1) or 18..26 (e_z = +1), each nx*ny contiguous values. One strided 2D copy
+// moves the 9 planes (source pitch = the buffer's direction stride).
+size_t cmlbm_halo_bytes(const cmlbm_t* h) { return h && h->ghost ? (size_t)9 * h->ghost * h->esize : 0; }
+
+static int halo_copy(cmlbm* h, int face, void* msg, const void* cmsg, int where, bool pack) {
+    if (!h) return CMLBM_ERR_INVALID;
+    if (!h->ghost) return fail(h, CMLBM_ERR_INVALID, "the handle is not a slab (bc[2] != CMLBM_HALO)");
+    if (face != CMLBM_FACE_BOTTOM && face != CMLBM_FACE_TOP) return fail(h, CMLBM_ERR_INVALID, "bad face");
+    if (where != CMLBM_DEVICE && where != CMLBM_HOST) return fail(h, CMLBM_ERR_INVALID, "bad `where`");
+    if (pack ? !msg : !cmsg) return fail(h, CMLBM_ERR_INVALID, "message buffer is NULL");
+    DeviceGuard g(h->cfg.device);
+    const size_t plane = h->ghost;                 // nx * ny
+    const size_t pitch = (size_t)h->p.S * h->esize;
+    const size_t width = plane * h->esize;
+    // buffer plane index (0 = ghost below, 1 .. nz own planes, nz + 1 = ghost above)
+    int dir0, zplane;
+    if (pack) {
+        dir0 = (face == CMLBM_FACE_TOP) ? 18 : 0;            // populations leaving through the face
+        zplane = (face == CMLBM_FACE_TOP) ? h->p.nz : 1;
+    } else {
+        dir0 = (face == CMLBM_FACE_BOTTOM) ? 18 : 0;         // populations entering through the face
+        zplane = (face == CMLBM_FACE_BOTTOM) ? 0 : h->p.nz + 1;
+    }
+    char* state = (char*)h->buf[h->cur] + ((size_t)dir0 * h->p.S + (size_t)zplane * plane) * h->esize;
+    cudaError_t e;
+    if (pack)
+        e = cudaMemcpy2DAsync(msg, width, state, pitch, width, 9,
+                              where == CMLBM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->st);
+    else
+        e = cudaMemcpy2DAsync(state, pitch, cmsg, width, width, 9,
+                              where == CMLBM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->st);
+    if (e != cudaSuccess) return cuda_fail(h, e, pack ? "face pack" : "face unpack");
+    if (where == CMLBM_HOST && (e = cudaStreamSynchronize(h->st)) != cudaSuccess)
+        return cuda_fail(h, e, pack ? "face pack" : "face unpack");
+    return CMLBM_OK;
+}
+
+int cmlbm_halo_pack(cmlbm_t* h, int face, void* out, int where) { return halo_copy(h, face, out, nullptr, where, true); }
+
+int cmlbm_halo_unpack(cmlbm_t* h, int face, const void* in, int where) {
+    return halo_copy(h, face, nullptr, in, where, false);
 }
 
 }  // extern "C"

@@ -36,13 +36,14 @@ template <int N, class F> __host__ __device__ __forceinline__ void sfor(F&& f) {
 // ------------------------------------------------------------------------------------------
 struct Params {
     int nx, ny, nz;
-    int bc[3];             // 0 periodic, 1 half-way bounce-back
+    int bc[3];             // 0 periodic, 1 half-way bounce-back, 2 slab with ghost planes (z only)
     int les;               // Smagorinsky eddy viscosity on
     int vd;                // van Driest damping on (y walls)
     int attractor;         // 0 Maxwellian, 1 factorized
     int reduced;           // reduced compressibility (u = j / rho0)
     int has_field;         // per-cell force field present
-    long long N;
+    long long N;           // cells updated (nx ny nz)
+    long long S;           // elements between direction planes of a state buffer (N, or nx ny (nz + 2) on a slab)
     double uw[3][2][3];    // wall velocities [axis][side][component]
     double F[3];           // uniform force
     double tau0;           // 1 / omega_nu (base)
@@ -59,7 +60,9 @@ template <class R> struct PR {
     int nx, ny, nz;
     int bc[3];
     int les, vd, attractor, reduced, has_field;
-    unsigned N;
+    unsigned N;            // cells (also the stride of force and moment fields)
+    unsigned S;            // direction-plane stride of a state buffer
+    int wz;                // z wrap length: nz, or 0 on a slab (the ghost planes are read instead)
     R uw[3][2][3];
     R F[3];
     R tau0, omega_bulk, omega3, omega4, cs, vd_aplus, vd_utau_nu, rho0;
@@ -71,6 +74,8 @@ template <class R> inline PR<R> typed(const Params& p) {
     for (int a = 0; a < 3; ++a) q.bc[a] = p.bc[a];
     q.les = p.les; q.vd = p.vd; q.attractor = p.attractor; q.reduced = p.reduced; q.has_field = p.has_field;
     q.N = (unsigned)p.N;
+    q.S = (unsigned)p.S;
+    q.wz = p.bc[2] == 2 ? 0 : p.nz;
     for (int a = 0; a < 3; ++a)
         for (int s = 0; s < 2; ++s)
             for (int d = 0; d < 3; ++d) q.uw[a][s][d] = (R)p.uw[a][s][d];
@@ -218,23 +223,26 @@ template <int D, class S, bool WALLS>
 __device__ __forceinline__ void gather_impl(const S* __restrict__ src, int x, int y, int z, const PR<typename Codec<S>::R>& p,
                                        typename Codec<S>::R (&h)[Lat<D>::Q]) {
     using R = typename Codec<S>::R;
-    const unsigned N = p.N;                  // Q * N < 2^32 is checked at create
+    // Q * S < 2^32 is checked at create. On a slab, row offsets of the ghost plane below are
+    // negative; they only occur for e_z = +1 (directions 18..26), so i * S + row stays >= 0 and
+    // the 32-bit unsigned sum is the exact offset.
+    const unsigned PS = p.S;
     int xs[3], ys[3], zs[3];
     bool xo[3] = {false, false, false}, yo[3] = {false, false, false}, zo[3] = {false, false, false};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {          // slot k <-> e = k - 1, source coordinate = x - e
         int sx = x + 1 - k, sy = y + 1 - k, sz = z + 1 - k;
         if (sx < 0 || sx >= p.nx) {
-            if (!WALLS || p.bc[0] == 0) sx += (sx < 0) ? p.nx : -p.nx;
+            if (!WALLS || p.bc[0] != 1) sx += (sx < 0) ? p.nx : -p.nx;
             else { xo[k] = true; sx = x; }
         }
         if (sy < 0 || sy >= p.ny) {
-            if (!WALLS || p.bc[1] == 0) sy += (sy < 0) ? p.ny : -p.ny;
+            if (!WALLS || p.bc[1] != 1) sy += (sy < 0) ? p.ny : -p.ny;
             else { yo[k] = true; sy = y; }
         }
         if constexpr (D == 3) {
             if (sz < 0 || sz >= p.nz) {
-                if (!WALLS || p.bc[2] == 0) sz += (sz < 0) ? p.nz : -p.nz;
+                if (!WALLS || p.bc[2] != 1) sz += (sz < 0) ? p.wz : -p.wz;
                 else { zo[k] = true; sz = z; }
             }
         } else {
@@ -259,8 +267,8 @@ __device__ __forceinline__ void gather_impl(const S* __restrict__ src, int x, in
             // issue back to back; the moving-wall term is added only where a wall was crossed
             const bool bx = xo[a], by = yo[b], bz = zo[c];
             const bool bounced = bx || by || bz;
-            const unsigned own = Lat<D>::opp(i) * N + cell;
-            const unsigned pulled = i * N + row[c][b] + (unsigned)xs[a];
+            const unsigned own = Lat<D>::opp(i) * PS + cell;
+            const unsigned pulled = i * PS + row[c][b] + (unsigned)xs[a];
             R d = Codec<S>::ld(src + (bounced ? own : pulled));
             constexpr int sx = (a == 2) ? 0 : 1, sy = (b == 2) ? 0 : 1, sz = (c == 2) ? 0 : 1;
             R eu = R(0);
@@ -272,7 +280,7 @@ __device__ __forceinline__ void gather_impl(const S* __restrict__ src, int x, in
             d += R(6) * eu * inv_cnt;
             h[slot<D>(i)] = d * w;
         } else {
-            h[slot<D>(i)] = Codec<S>::ld(src + (i * N + row[c][b] + (unsigned)xs[a])) * w;
+            h[slot<D>(i)] = Codec<S>::ld(src + (i * PS + row[c][b] + (unsigned)xs[a])) * w;
         }
     });
 }
@@ -285,8 +293,8 @@ template <int D, class S, bool WALLS>
 __device__ __forceinline__ void gather(const S* __restrict__ src, int x, int y, int z, const PR<typename Codec<S>::R>& p,
                                        typename Codec<S>::R (&h)[Lat<D>::Q]) {
     if constexpr (WALLS) {
-        const bool near = (p.bc[0] && (x == 0 || x == p.nx - 1)) || (p.bc[1] && (y == 0 || y == p.ny - 1)) ||
-                          (D == 3 && p.bc[2] && (z == 0 || z == p.nz - 1));
+        const bool near = (p.bc[0] == 1 && (x == 0 || x == p.nx - 1)) || (p.bc[1] == 1 && (y == 0 || y == p.ny - 1)) ||
+                          (D == 3 && p.bc[2] == 1 && (z == 0 || z == p.nz - 1));
         if (near) gather_impl<D, S, true>(src, x, y, z, p, h);
         else gather_impl<D, S, false>(src, x, y, z, p, h);
     } else {

@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S>()) k_step(const S* 
     const int z = blockIdx.z;
     if (x >= p.nx || y >= p.ny) return;
     const unsigned cell = (unsigned)((z * p.ny + y) * p.nx + x);
-    const unsigned N = p.N;
+    const unsigned PS = p.S;
     R h[Q];
     gather<D, S, FT::WALLS>(src, x, y, z, p, h);
     R F[3];
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S>()) k_step(const S* 
     sfor<Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         constexpr R iw = (R)inv_weight<D>(i);
-        Codec<S>::st(dst + (i * N + cell), h[slot<D>(i)] * iw);
+        Codec<S>::st(dst + (i * PS + cell), h[slot<D>(i)] * iw);
     });
 }
 
@@ -120,27 +120,31 @@ __global__ void __launch_bounds__(kBlock) k_equilibrium(S* __restrict__ dst, con
     sfor<Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         constexpr R iw = (R)inv_weight<D>(i);
-        Codec<S>::st(dst + ((unsigned)i * p.N + cell), m[slot<D>(i)] * iw);
+        Codec<S>::st(dst + ((unsigned)i * p.S + cell), m[slot<D>(i)] * iw);
     });
 }
 
-// s_i(x) = fbar_i(x + e_i), or the reflected value when x + e_i is behind a wall
+// s_i(x) = fbar_i(x + e_i), or the reflected value when x + e_i is behind a wall. On a slab
+// (bc[2] == 2) the grid's z index runs over the ghost planes too (z = -1 .. nz); an entry whose
+// x + e_i lies outside the slab's own planes is left unwritten: it is never pulled by this
+// slab, and the neighbour holds the same value in its own ghost plane.
 template <int D, class S>
 __global__ void __launch_bounds__(kBlock) k_unstream(const S* __restrict__ fb, S* __restrict__ dst, PR<typename Codec<S>::R> p) {
     using R = typename Codec<S>::R;
     constexpr int Q = Lat<D>::Q;
+    const bool slab = p.bc[2] == 2;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
+    const int z = (int)blockIdx.z - (slab ? 1 : 0);
     if (x >= p.nx || y >= p.ny) return;
-    const unsigned cell = (unsigned)((z * p.ny + y) * p.nx + x);
+    const long long cell = ((long long)z * p.ny + y) * p.nx + x;
     const int xyz[3] = {x, y, z};
     const int n[3] = {p.nx, p.ny, p.nz};
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int e[3] = {Lat<D>::ex(i), Lat<D>::ey(i), Lat<D>::ez(i)};
         int t[3];
-        bool out = false;
+        bool out = false, beyond = false;
         R wsum[3] = {0, 0, 0}, cnt = 0;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -148,6 +152,8 @@ __global__ void __launch_bounds__(kBlock) k_unstream(const S* __restrict__ fb, S
             if (t[a] < 0 || t[a] >= n[a]) {
                 if (p.bc[a] == 0) {
                     t[a] += (t[a] < 0) ? n[a] : -n[a];
+                } else if (p.bc[a] == 2) {
+                    beyond = true;      // x + e_i is in a neighbouring slab
                 } else {
                     const int side = (t[a] < 0) ? 0 : 1;
                     out = true;
@@ -159,15 +165,19 @@ __global__ void __launch_bounds__(kBlock) k_unstream(const S* __restrict__ fb, S
                 }
             }
         }
+        // A reflected entry is pulled by its own cell: written for the slab's own planes only. A
+        // plain entry is pulled by the cell x + e_i: written when that cell is one of the slab's.
+        const bool ghost = z < 0 || z >= p.nz;
+        if (out ? ghost : beyond) continue;
         R d;
         if (out) {
             const R eu = (R)e[0] * wsum[0] + (R)e[1] * wsum[1] + (R)e[2] * wsum[2];
-            d = Codec<S>::ld(fb + (long long)Lat<D>::opp(i) * p.N + cell) + R(6) * eu / cnt;
+            d = Codec<S>::ld(fb + (long long)Lat<D>::opp(i) * p.S + cell) + R(6) * eu / cnt;
         } else {
-            const unsigned tc = (unsigned)((t[2] * p.ny + t[1]) * p.nx + t[0]);
-            d = Codec<S>::ld(fb + (long long)i * p.N + tc);
+            const long long tc = ((long long)t[2] * p.ny + t[1]) * p.nx + t[0];
+            d = Codec<S>::ld(fb + (long long)i * p.S + tc);
         }
-        Codec<S>::st(dst + (long long)i * p.N + cell, d);
+        Codec<S>::st(dst + (long long)i * p.S + cell, d);
     }
 }
 
@@ -262,7 +272,7 @@ __global__ void k_convert_force(const double* __restrict__ in, R* __restrict__ o
 // ------------------------------------------------------------------------------------------
 // Host launchers (instantiated in inst_*.cu)
 // ------------------------------------------------------------------------------------------
-inline bool has_walls(const Params& p) { return p.bc[0] || p.bc[1] || p.bc[2]; }
+inline bool has_walls(const Params& p) { return p.bc[0] == 1 || p.bc[1] == 1 || p.bc[2] == 1; }
 
 template <int D, class S, class FT>
 void launch_step_ft(const void* src, void* dst, const void* Ff, const Params& p, cudaStream_t st) {
@@ -311,7 +321,9 @@ cudaError_t launch_init(void* tmp, void* dst, const void* Ff, const Params& p, c
     using R = typename Codec<S>::R;
     const dim3 b = cell_block(p.nx), g = cell_grid(p, b);
     k_equilibrium<D, S><<<g, b, 0, st>>>((S*)tmp, (const R*)Ff, typed<R>(p), rho, u);
-    k_unstream<D, S><<<g, b, 0, st>>>((const S*)tmp, (S*)dst, typed<R>(p));
+    dim3 gu = g;
+    if (p.bc[2] == 2) gu.z += 2;      // slab: the ghost planes receive the entries leaving the slab
+    k_unstream<D, S><<<gu, b, 0, st>>>((const S*)tmp, (S*)dst, typed<R>(p));
     return cudaGetLastError();
 }
 

@@ -153,6 +153,7 @@ int cmlbm_reduce_noalloc(const cmlbm_config* cfg, const void* state, const doubl
     p.ny = c.ny;
     p.nz = c.nz;
     p.N = N;
+    p.S = N;
     for (int a = 0; a < 3; ++a) p.bc[a] = c.bc[a];
     std::memcpy(p.uw, c.wall_velocity, sizeof(p.uw));
     for (int d = 0; d < 3; ++d) p.F[d] = uniform_force ? uniform_force[d] : 0.0;

@@ -54,6 +54,9 @@ def test_config_struct_size_matches(lib):
     (dict(nx=1024, ny=1024, nz=200), "2^32"),
     (dict(attractor=3), "attractor"),
     (dict(reduced_compressibility=True, rho0=0.0), "rho0"),
+    (dict(bc=("halo", "periodic", "periodic")), "CMLBM_HALO on z"),
+    (dict(lattice="D2Q9", nz=1, bc=("periodic", "periodic", "halo")), "CMLBM_HALO needs D3Q27"),
+    (dict(nx=1024, ny=1024, nz=151, bc=("periodic", "periodic", "halo")), "(nz+2)"),
 ])
 def test_invalid_configs_are_rejected_without_a_gpu(lib, kw, msg):
     c = lib.make_config(**kw)
@@ -65,8 +68,19 @@ def test_invalid_configs_are_rejected_without_a_gpu(lib, kw, msg):
     assert msg in so.cmlbm_last_error(None).decode()
 
 
+def test_tma_on_a_slab_is_unsupported_without_a_gpu(lib):
+    c = lib.make_config(nx=128, ny=4, nz=4, bc=("periodic", "periodic", "halo"), kernel="tma")
+    h = ctypes.c_void_p()
+    so = lib.load()
+    assert so.cmlbm_create(ctypes.byref(c), ctypes.byref(h)) == lib.ERR_UNSUPPORTED
+    assert "slab" in so.cmlbm_last_error(None).decode()
+
+
 def test_null_handle_calls_fail_cleanly(lib):
     so = lib.load()
+    assert so.cmlbm_halo_bytes(None) == 0
+    assert so.cmlbm_halo_pack(None, 0, None, 0) == lib.ERR_INVALID
+    assert so.cmlbm_halo_unpack(None, 0, None, 0) == lib.ERR_INVALID
     assert so.cmlbm_step(None, 1) == lib.ERR_INVALID
     assert so.cmlbm_state_bytes(None) == 0
     assert so.cmlbm_launch_count(None) == 0
