@@ -50,8 +50,9 @@ def parse():
     ap.add_argument("--form-steps", type=int, default=40)
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"],
                     help="population storage of the timed Taylor-Green step (f32 is the headline)")
-    ap.add_argument("--kernel", default="auto", choices=["auto", "direct", "tma"],
-                    help="step kernel: direct loads (auto) or the TMA-staged variant")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "direct", "pair", "tma"],
+                    help="step kernel: the library's choice (auto), one cell per thread (direct), two cells "
+                         "per thread in packed FP32 (pair), or rows staged by TMA (tma)")
     return ap.parse_args()
 
 
@@ -224,8 +225,9 @@ def run_tgv(cm, n, storage, steps, warmup, dist, clocks=None, kernel="auto"):
     ms, launches = time_steps(s, steps, warmup, dist, stream)
     ck = clocks.stop() if clocks else None
     red = s.reduce()
+    kernel_used = s.step_kernel
     s.close()
-    return ms, launches, ck, red
+    return ms, launches, ck, red, kernel_used
 
 
 def run_hit_les(cm, n, storage, steps, warmup, dist):
@@ -353,13 +355,12 @@ def our_arm(args, dist):
     pk, pk_kind = peaks()
     clocks = Clocks(dist.local)
     st = args.storage
-    ms, launches, ck, red = run_tgv(cm, n, st, args.steps, args.warmup, dist, clocks, kernel=args.kernel)
+    ms, launches, ck, red, kname = run_tgv(cm, n, st, args.steps, args.warmup, dist, clocks, kernel=args.kernel)
     ms = dist.max(ms)
     per_launch_s = ms / 1e3 / args.steps
     value = dist.world * N * args.steps / (ms / 1e3) / 1e6
     bpc = BYTES_PER_CELL[("D3Q27", st)]
     achieved = bpc * N / per_launch_s / 1e9
-    kname = "tma" if args.kernel == "tma" else "direct"
     traffic_pc = measured_traffic(f"k_step_d3q27_{st}_periodic_{kname}")
     line = {
         "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": dist.world, "steps": args.steps,
@@ -374,7 +375,8 @@ def our_arm(args, dist):
                      "frac": achieved / pk["hbm_gbs"], "peak_kind": pk_kind,
                      "traffic": None if traffic_pc is None else traffic_pc * N,
                      "algorithmic_bytes_per_cell": bpc,
-                     "kernel": f"k_step{'_tma' if kname == 'tma' else ''}<D3Q27,{st},periodic>"},
+                     "kernel": {"tma": "k_step_tma", "pair": "k_step_pair", "direct": "k_step"}[kname]
+                               + f"<D3Q27,{st},periodic>"},
         "clocks": ck,
         "gpu_launches": int(launches),
         "diagnostics": {"mass": red[0], "kinetic_energy": red[4]},
@@ -386,7 +388,7 @@ def our_arm(args, dist):
         if not args.no_forms:
             fs = args.form_steps
             for st in ("bf16", "f16"):
-                m, l, _, _ = run_tgv(cm, n, st, fs, 3, Dist0())
+                m, l, _, _, _ = run_tgv(cm, n, st, fs, 3, Dist0())
                 sec = m / 1e3 / fs
                 forms[f"tgv{n}_{st}"] = {"MLUPS": N / sec / 1e6, "hbm_frac": BYTES_PER_CELL[("D3Q27", st)] * N / sec / 1e9
                                          / pk["hbm_gbs"], "steps": fs}

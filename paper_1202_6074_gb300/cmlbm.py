@@ -31,7 +31,8 @@ SYMBOLS = ["cmlbm_config_default", "cmlbm_create", "cmlbm_destroy", "cmlbm_last_
            "cmlbm_moments_of", "cmlbm_reduce", "cmlbm_state_bytes", "cmlbm_get_state", "cmlbm_set_state",
            "cmlbm_adjoint_terminal", "cmlbm_step_adjoint", "cmlbm_launch_count", "cmlbm_reduce_noalloc",
            "cmlbm_turbulence_force", "cmlbm_step_filtered", "cmlbm_halo_bytes", "cmlbm_halo_pack",
-           "cmlbm_halo_unpack"]
+           "cmlbm_halo_unpack", "cmlbm_step_kernel"]
+KERNELS = {0: "auto", 1: "direct", 2: "tma", 3: "pair"}
 
 
 class Config(ctypes.Structure):
@@ -100,6 +101,7 @@ def load():
         "cmlbm_halo_bytes": (ctypes.c_size_t, [P]),
         "cmlbm_halo_pack": (I, [P, I, P, I]),
         "cmlbm_halo_unpack": (I, [P, I, P, I]),
+        "cmlbm_step_kernel": (I, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -154,7 +156,7 @@ def make_config(lattice="D3Q27", nx=32, ny=32, nz=32, storage="f32", bc=("period
     c.rho0 = float(rho0)
     c.device = int(device)
     c.stream = stream
-    c.kernel = {"auto": 0, "direct": 1, "tma": 2}[kernel] if isinstance(kernel, str) else int(kernel)
+    c.kernel = {"auto": 0, "direct": 1, "tma": 2, "pair": 3}[kernel] if isinstance(kernel, str) else int(kernel)
     return c
 
 
@@ -210,6 +212,11 @@ class Solver:
     @property
     def launch_count(self):
         return int(self.lib.cmlbm_launch_count(self.h))
+
+    @property
+    def step_kernel(self):
+        """"direct", "pair" or "tma": the step kernel this handle runs."""
+        return KERNELS[int(self.lib.cmlbm_step_kernel(self.h))]
 
     # ---- API --------------------------------------------------------------------------
     def set_force(self, uniform=(0.0, 0.0, 0.0), field=None):

@@ -184,6 +184,7 @@ int cmlbm_create(const cmlbm_config* cfg, cmlbm_t** out) {
         if (c.bc[a] != CMLBM_PERIODIC && c.bc[a] != CMLBM_BOUNCEBACK && !(a == 2 && c.bc[a] == CMLBM_HALO))
             return fail(nullptr, CMLBM_ERR_INVALID,
                         "bc must be CMLBM_PERIODIC or CMLBM_BOUNCEBACK (or CMLBM_HALO on z)");
+    if (c.kernel < CMLBM_KERNEL_AUTO || c.kernel > CMLBM_KERNEL_PAIR) return fail(nullptr, CMLBM_ERR_INVALID, "unknown kernel");
     const bool slab = c.bc[2] == CMLBM_HALO;
     if (slab && c.lattice != CMLBM_D3Q27) return fail(nullptr, CMLBM_ERR_INVALID, "CMLBM_HALO needs D3Q27");
     const long long S = slab ? (long long)c.nx * c.ny * (c.nz + 2) : N;
@@ -257,6 +258,16 @@ int cmlbm_create(const cmlbm_config* cfg, cmlbm_t** out) {
         return fail(nullptr, CMLBM_ERR_NOMEM, "cudaMalloc of the reduction buffers failed");
     }
     if (cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess) h->nsm = 1;
+    if (c.kernel == CMLBM_KERNEL_AUTO && cm::pair_eligible(p, h->D, c.storage != CMLBM_F64)) p.pair = 1;
+    if (c.kernel == CMLBM_KERNEL_PAIR) {
+        if (!cm::pair_eligible(p, h->D, c.storage != CMLBM_F64)) {
+            cmlbm_destroy(h);
+            return fail(nullptr, CMLBM_ERR_UNSUPPORTED,
+                        "the two-cells-per-thread step needs D3Q27, FP32/BF16/FP16 storage, periodic x, nx a "
+                        "multiple of 64 and the standard collision");
+        }
+        p.pair = 1;
+    }
     if (c.kernel == CMLBM_KERNEL_TMA) {
         const bool eligible = h->D == 3 && c.storage != CMLBM_F64 && c.attractor == CMLBM_ATTRACTOR_MAXWELL &&
                               !c.reduced_compressibility;
@@ -307,6 +318,12 @@ int cmlbm_set_stream(cmlbm_t* h, void* stream) {
 }
 
 long long cmlbm_launch_count(const cmlbm_t* h) { return h ? h->launches : 0; }
+
+int cmlbm_step_kernel(const cmlbm_t* h) {
+    if (!h) return CMLBM_ERR_INVALID;
+    if (h->tma) return CMLBM_KERNEL_TMA;
+    return h->p.pair ? CMLBM_KERNEL_PAIR : CMLBM_KERNEL_DIRECT;
+}
 
 size_t cmlbm_state_bytes(const cmlbm_t* h) { return h ? (size_t)h->Q * (size_t)h->p.S * h->esize : 0; }
 

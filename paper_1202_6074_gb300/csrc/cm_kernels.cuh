@@ -72,6 +72,105 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S>()) k_step(const S* 
     });
 }
 
+// ---- two cells of a row per thread -------------------------------------------------------------
+// Cells (x, y, z) and (x + nx/2, y, z) are updated together with the packed FP32 instructions
+// (R = F2). They share y and z, hence the y/z wall flags, the row offsets, and the van Driest
+// constant; x must be periodic. Each lane is rounded as the scalar FP32 arithmetic rounds it.
+#ifndef CM_PAIR_MIN_BLOCKS
+#define CM_PAIR_MIN_BLOCKS 4
+#endif
+template <class S, bool WALLS>
+__device__ __forceinline__ void gather_pair(const S* __restrict__ src, int x, int y, int z, const PR<float>& p, F2 (&h)[27]) {
+    const unsigned PS = p.S;
+    const int half = p.nx >> 1;
+    int xa[3], xb[3], ys[3], zs[3];
+    bool yo[3] = {false, false, false}, zo[3] = {false, false, false};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {          // slot k <-> e = k - 1, source coordinate = x - e
+        int sa = x + 1 - k, sb = x + half + 1 - k;     // sa in [-1, half], sb in [half - 1, nx]
+        if (sa < 0) sa += p.nx;
+        if (sb >= p.nx) sb -= p.nx;
+        xa[k] = sa;
+        xb[k] = sb;
+        int sy = y + 1 - k, sz = z + 1 - k;
+        if (sy < 0 || sy >= p.ny) {
+            if (!WALLS || p.bc[1] != 1) sy += (sy < 0) ? p.ny : -p.ny;
+            else { yo[k] = true; sy = y; }
+        }
+        if (sz < 0 || sz >= p.nz) {
+            if (!WALLS || p.bc[2] != 1) sz += (sz < 0) ? p.wz : -p.wz;
+            else { zo[k] = true; sz = z; }
+        }
+        ys[k] = sy;
+        zs[k] = sz;
+    }
+    const unsigned cellA = (unsigned)((z * p.ny + y) * p.nx + x), cellB = cellA + (unsigned)half;
+    unsigned row[3][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) row[c][b] = (unsigned)((zs[c] * p.ny + ys[b]) * p.nx);
+    sfor<27>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int a = Lat<3>::ex(i) + 1, b = Lat<3>::ey(i) + 1, c = Lat<3>::ez(i) + 1;
+        constexpr float w = (float)weight<3>(i);
+        const unsigned base = i * PS + row[c][b];
+        if constexpr (WALLS) {
+            const bool by = yo[b], bz = zo[c];
+            const bool bounced = by || bz;
+            const unsigned own = Lat<3>::opp(i) * PS;
+            const float da = Codec<S>::ld(src + (bounced ? own + cellA : base + (unsigned)xa[a]));
+            const float db = Codec<S>::ld(src + (bounced ? own + cellB : base + (unsigned)xb[a]));
+            constexpr int sy = (b == 2) ? 0 : 1, sz = (c == 2) ? 0 : 1;
+            float eu = 0.f;
+            if constexpr (b != 1) eu += by ? (float(Lat<3>::ex(i)) * p.uw[1][sy][0] + float(Lat<3>::ey(i)) * p.uw[1][sy][1] + float(Lat<3>::ez(i)) * p.uw[1][sy][2]) : 0.f;
+            if constexpr (c != 1) eu += bz ? (float(Lat<3>::ex(i)) * p.uw[2][sz][0] + float(Lat<3>::ey(i)) * p.uw[2][sz][1] + float(Lat<3>::ez(i)) * p.uw[2][sz][2]) : 0.f;
+            const int cnt = (int)by + (int)bz;
+            const float add = 6.f * eu * (cnt == 2 ? 0.5f : 1.f);
+            h[slot<3>(i)] = F2(da + add, db + add) * F2(w);
+        } else {
+            h[slot<3>(i)] = F2(Codec<S>::ld(src + (base + (unsigned)xa[a])), Codec<S>::ld(src + (base + (unsigned)xb[a]))) * F2(w);
+        }
+    });
+}
+
+template <class S, class FT>
+__global__ void __launch_bounds__(kBlock, CM_PAIR_MIN_BLOCKS) k_step_pair(const S* __restrict__ src, S* __restrict__ dst,
+                                                                          const float* __restrict__ Ff, PR<float> p) {
+    const int half = p.nx >> 1;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= half || y >= p.ny) return;
+    const unsigned cellA = (unsigned)((z * p.ny + y) * p.nx + x), cellB = cellA + (unsigned)half;
+    const unsigned PS = p.S;
+    F2 h[27];
+    if constexpr (FT::WALLS) {
+        const bool near = (p.bc[1] == 1 && (y == 0 || y == p.ny - 1)) || (p.bc[2] == 1 && (z == 0 || z == p.nz - 1));
+        if (near) gather_pair<S, true>(src, x, y, z, p, h);
+        else gather_pair<S, false>(src, x, y, z, p, h);
+    } else {
+        gather_pair<S, false>(src, x, y, z, p, h);
+    }
+    F2 F[3];
+    if (FT::FIELD && p.has_field) {
+        const unsigned N = p.N;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) F[d] = F2(__ldg(Ff + (d * N + cellA)), __ldg(Ff + (d * N + cellB)));
+    } else {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) F[d] = F2(p.F[d]);
+    }
+    collide<3, F2, FT>(h, F, p, smagorinsky_constant<float, FT::LES>(p, y));
+    sfor<27>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr float iw = (float)inv_weight<3>(i);
+        const F2 v = h[slot<3>(i)] * F2(iw);
+        Codec<S>::st(dst + (i * PS + cellA), v.v.x);
+        Codec<S>::st(dst + (i * PS + cellB), v.v.y);
+    });
+}
+
 // ---- density and velocity of the pulled field ----------------------------------------------
 template <int D, class S, bool WALLS>
 __global__ void __launch_bounds__(kBlock) k_moments(const S* __restrict__ src, const typename Codec<S>::R* __restrict__ Ff,
@@ -92,92 +191,6 @@ __global__ void __launch_bounds__(kBlock) k_moments(const S* __restrict__ src, c
         u[cell] = (double)hy.ux;
         u[p.N + cell] = (double)hy.uy;
         u[2 * p.N + cell] = (double)hy.uz;
-    }
-}
-
-// ---- initial state: equilibrium at the cell, then the inverse of the pull -----------------
-template <int D, class S>
-__global__ void __launch_bounds__(kBlock) k_equilibrium(S* __restrict__ dst, const typename Codec<S>::R* __restrict__ Ff,
-                                                       PR<typename Codec<S>::R> p, const double* __restrict__ rho, const double* __restrict__ u) {
-    using R = typename Codec<S>::R;
-    constexpr int Q = Lat<D>::Q;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    if (x >= p.nx || y >= p.ny) return;
-    const unsigned cell = (unsigned)((z * p.ny + y) * p.nx + x);
-    R F[3];
-    load_force<R>(Ff, p, cell, F);
-    const double r = rho ? rho[cell] : 1.0;
-    double ux = u ? u[cell] : 0.0, uy = u ? u[p.N + cell] : 0.0, uz = (u && D == 3) ? u[2 * p.N + cell] : 0.0;
-    if (p.reduced) {   // momentum rho0 u: centre the equilibrium on rho0 u / rho
-        ux *= (double)p.rho0 / r;
-        uy *= (double)p.rho0 / r;
-        uz *= (double)p.rho0 / r;
-    }
-    R m[Q];
-    equilibrium<D, R>(m, (R)r, (R)ux, (R)uy, (R)uz, F);
-    sfor<Q>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        constexpr R iw = (R)inv_weight<D>(i);
-        Codec<S>::st(dst + ((unsigned)i * p.S + cell), m[slot<D>(i)] * iw);
-    });
-}
-
-// s_i(x) = fbar_i(x + e_i), or the reflected value when x + e_i is behind a wall. On a slab
-// (bc[2] == 2) the grid's z index runs over the ghost planes too (z = -1 .. nz); an entry whose
-// x + e_i lies outside the slab's own planes is left unwritten: it is never pulled by this
-// slab, and the neighbour holds the same value in its own ghost plane.
-template <int D, class S>
-__global__ void __launch_bounds__(kBlock) k_unstream(const S* __restrict__ fb, S* __restrict__ dst, PR<typename Codec<S>::R> p) {
-    using R = typename Codec<S>::R;
-    constexpr int Q = Lat<D>::Q;
-    const bool slab = p.bc[2] == 2;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = (int)blockIdx.z - (slab ? 1 : 0);
-    if (x >= p.nx || y >= p.ny) return;
-    const long long cell = ((long long)z * p.ny + y) * p.nx + x;
-    const int xyz[3] = {x, y, z};
-    const int n[3] = {p.nx, p.ny, p.nz};
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const int e[3] = {Lat<D>::ex(i), Lat<D>::ey(i), Lat<D>::ez(i)};
-        int t[3];
-        bool out = false, beyond = false;
-        R wsum[3] = {0, 0, 0}, cnt = 0;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            t[a] = xyz[a] + e[a];
-            if (t[a] < 0 || t[a] >= n[a]) {
-                if (p.bc[a] == 0) {
-                    t[a] += (t[a] < 0) ? n[a] : -n[a];
-                } else if (p.bc[a] == 2) {
-                    beyond = true;      // x + e_i is in a neighbouring slab
-                } else {
-                    const int side = (t[a] < 0) ? 0 : 1;
-                    out = true;
-                    cnt += 1;
-                    wsum[0] += p.uw[a][side][0];
-                    wsum[1] += p.uw[a][side][1];
-                    wsum[2] += p.uw[a][side][2];
-                    t[a] = xyz[a];
-                }
-            }
-        }
-        // A reflected entry is pulled by its own cell: written for the slab's own planes only. A
-        // plain entry is pulled by the cell x + e_i: written when that cell is one of the slab's.
-        const bool ghost = z < 0 || z >= p.nz;
-        if (out ? ghost : beyond) continue;
-        R d;
-        if (out) {
-            const R eu = (R)e[0] * wsum[0] + (R)e[1] * wsum[1] + (R)e[2] * wsum[2];
-            d = Codec<S>::ld(fb + (long long)Lat<D>::opp(i) * p.S + cell) + R(6) * eu / cnt;
-        } else {
-            const long long tc = ((long long)t[2] * p.ny + t[1]) * p.nx + t[0];
-            d = Codec<S>::ld(fb + (long long)i * p.S + tc);
-        }
-        Codec<S>::st(dst + (long long)i * p.S + cell, d);
     }
 }
 
@@ -277,6 +290,15 @@ inline bool has_walls(const Params& p) { return p.bc[0] == 1 || p.bc[1] == 1 || 
 template <int D, class S, class FT>
 void launch_step_ft(const void* src, void* dst, const void* Ff, const Params& p, cudaStream_t st) {
     using R = typename Codec<S>::R;
+    if constexpr (D == 3 && sizeof(R) == 4 && !FT::GEN) {
+        if (p.pair) {
+            const int half = p.nx / 2;
+            const dim3 b = cell_block(half);
+            const dim3 g((half + b.x - 1) / b.x, (p.ny + b.y - 1) / b.y, p.nz);
+            k_step_pair<S, FT><<<g, b, 0, st>>>((const S*)src, (S*)dst, (const float*)Ff, typed<float>(p));
+            return;
+        }
+    }
     const dim3 b = cell_block(p.nx), g = cell_grid(p, b);
     k_step<D, S, FT><<<g, b, 0, st>>>((const S*)src, (S*)dst, (const R*)Ff, typed<R>(p));
 }
@@ -315,18 +337,6 @@ cudaError_t launch_moments(const void* src, const void* Ff, const Params& p, dou
     return cudaGetLastError();
 }
 
-template <int D, class S>
-cudaError_t launch_init(void* tmp, void* dst, const void* Ff, const Params& p, const double* rho, const double* u,
-                        cudaStream_t st) {
-    using R = typename Codec<S>::R;
-    const dim3 b = cell_block(p.nx), g = cell_grid(p, b);
-    k_equilibrium<D, S><<<g, b, 0, st>>>((S*)tmp, (const R*)Ff, typed<R>(p), rho, u);
-    dim3 gu = g;
-    if (p.bc[2] == 2) gu.z += 2;      // slab: the ghost planes receive the entries leaving the slab
-    k_unstream<D, S><<<gu, b, 0, st>>>((const S*)tmp, (S*)dst, typed<R>(p));
-    return cudaGetLastError();
-}
-
 inline int reduce_blocks(const Params& p) {
     long long nb = (p.N + kRedThreads - 1) / kRedThreads;
     return (int)(nb < kRedMaxBlocks ? nb : kRedMaxBlocks);
@@ -345,6 +355,8 @@ cudaError_t launch_reduce(const void* src, const void* Ff, const Params& p, doub
 }
 
 }  // namespace cm
+
+#include "cm_init.cuh"
 
 // Explicit-instantiation helpers
 #define CM_INSTANTIATE(D, S)                                                                               \

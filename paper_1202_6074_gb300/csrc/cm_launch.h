@@ -28,6 +28,14 @@ cudaError_t launch_adjoint_step(const void* state, const void* Ff, const Params&
 
 constexpr int kReduceMaxBlocks = 1216;
 
+// The two-cells-per-thread step (k_step_pair) covers D3Q27 with FP32 arithmetic, periodic x,
+// nx a multiple of 64 (each warp's 32 lanes read 32 consecutive cells of both halves of the
+// row) and the standard collision (the factorized / reduced forms would spill at its register
+// budget).
+inline bool pair_eligible(const Params& p, int D, bool fp32_arith) {
+    return D == 3 && fp32_arith && p.bc[0] == 0 && p.nx % 64 == 0 && p.attractor == 0 && !p.reduced;
+}
+
 // turbulence as forcing (turbulence.cu): scratch holds 10 N arithmetic values
 template <int D, class S>
 cudaError_t launch_turbulence_force(const void* state, void* force, const Params& p, double cs, void* scratch,

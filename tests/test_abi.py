@@ -55,6 +55,7 @@ def test_config_struct_size_matches(lib):
     (dict(attractor=3), "attractor"),
     (dict(reduced_compressibility=True, rho0=0.0), "rho0"),
     (dict(bc=("halo", "periodic", "periodic")), "CMLBM_HALO on z"),
+    (dict(kernel=9), "unknown kernel"),
     (dict(lattice="D2Q9", nz=1, bc=("periodic", "periodic", "halo")), "CMLBM_HALO needs D3Q27"),
     (dict(nx=1024, ny=1024, nz=151, bc=("periodic", "periodic", "halo")), "(nz+2)"),
 ])
@@ -79,6 +80,7 @@ def test_tma_on_a_slab_is_unsupported_without_a_gpu(lib):
 def test_null_handle_calls_fail_cleanly(lib):
     so = lib.load()
     assert so.cmlbm_halo_bytes(None) == 0
+    assert so.cmlbm_step_kernel(None) == lib.ERR_INVALID
     assert so.cmlbm_halo_pack(None, 0, None, 0) == lib.ERR_INVALID
     assert so.cmlbm_halo_unpack(None, 0, None, 0) == lib.ERR_INVALID
     assert so.cmlbm_step(None, 1) == lib.ERR_INVALID

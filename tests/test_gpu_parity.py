@@ -382,6 +382,90 @@ def test_tma_requested_on_ineligible_config_is_rejected(cm):
     assert e.value.code == cm.ERR_UNSUPPORTED
 
 
+# D3Q27 cases the two-cells-per-thread kernel takes (periodic x, nx a multiple of 64)
+PAIR_CASES = {
+    "pair_periodic_field": dict(lattice="D3Q27", shape=(5, 7, 128), flow="tgv", kw=dict(tau=0.6, omega_bulk=1.0)),
+    "pair_walls_les_vd": dict(lattice="D3Q27", shape=(6, 9, 64), flow="channel",
+                              kw=dict(tau=0.52, smagorinsky_cs=0.15, van_driest=(26.0, 8.0),
+                                      bc=("periodic", "bounceback", "bounceback"),
+                                      wall_velocity=[[[0, 0, 0], [0, 0, 0]], [[0.02, 0, 0.01], [-0.03, 0.0, 0.0]],
+                                                     [[0.01, 0, 0], [0, 0.02, 0]]])),
+    "pair_bulk_follows_shear_les": dict(lattice="D3Q27", shape=(4, 6, 192), flow="tgv",
+                                        kw=dict(tau=0.51, smagorinsky_cs=0.12, omega_3=1.3, omega_4=0.9)),
+}
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("name", list(PAIR_CASES))
+def test_pair_kernel_one_step_elementwise(cm, name, storage):
+    case = PAIR_CASES[name]
+    rho, u, F = _inputs(case)
+    s, o = _pair(cm, case["lattice"], case["shape"], storage, rho, u, F, kernel="pair", **case["kw"])
+    s0 = s.get_state()
+    o.set_state(H.decode(s0, case["lattice"]))
+    s.step(1)
+    o.step(1)
+    got = H.decode(s.get_state(), case["lattice"])
+    w = H.lattice(case["lattice"]).w.view(-1, 1, 1, 1)
+    d_got, d_ref = got / w - 1, o.s / w - 1
+    tol = ONE_STEP_ATOL[storage] + ONE_STEP_RTOL[storage] * d_ref.abs()
+    err = (d_got - d_ref).abs()
+    assert bool((err <= tol).all()), f"max |dd| = {err.max().item():.3e}"
+    s.close()
+
+
+@pytest.mark.parametrize("name", list(PAIR_CASES))
+def test_pair_kernel_fp32_trajectory(cm, name):
+    case = PAIR_CASES[name]
+    rho, u, F = _inputs(case)
+    s, o = _pair(cm, case["lattice"], case["shape"], "f32", rho, u, F, kernel="pair", **case["kw"])
+    s.step(30)
+    o.step(30)
+    _, ug = s.moments()
+    _, uo = o.moments()
+    assert H.rel_l2(ug, uo) < 1e-5
+    s.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_pair_and_direct_kernels_agree(cm, storage):
+    case = PAIR_CASES["pair_walls_les_vd"]
+    rho, u, F = _inputs(case)
+    states = []
+    for kernel in ("pair", "direct"):
+        s, _ = _pair(cm, case["lattice"], case["shape"], storage, rho, u, F, kernel=kernel, **case["kw"])
+        s.step(15)
+        states.append(H.decode(s.get_state(), case["lattice"]))
+        s.close()
+    w = H.lattice(case["lattice"]).w.view(-1, 1, 1, 1)
+    diff = ((states[0] - states[1]) / w).abs().max().item()
+    assert diff < (1e-5 if storage == "f32" else 2e-2)
+
+
+@pytest.mark.parametrize("kw,expect", [
+    (dict(nx=128), "pair"), (dict(nx=128, storage="bf16"), "pair"), (dict(nx=96), "direct"),
+    (dict(nx=128, storage="f64"), "direct"), (dict(nx=128, attractor="factorized"), "direct"),
+    (dict(nx=128, bc=("bounceback", "periodic", "periodic")), "direct"), (dict(nx=128, kernel="direct"), "direct"),
+    (dict(nx=128, kernel="tma"), "tma"), (dict(nx=64, bc=("periodic", "periodic", "halo")), "pair")])
+def test_automatic_kernel_choice(cm, kw, expect):
+    args = dict(lattice="D3Q27", ny=4, nz=4, storage="f32")
+    args.update(kw)
+    s = cm.Solver(**args)
+    assert s.step_kernel == expect
+    s.close()
+
+
+@pytest.mark.parametrize("kw", [dict(nx=96), dict(nx=128, bc=("bounceback", "periodic", "periodic")),
+                                dict(nx=128, attractor="factorized"), dict(nx=128, storage="f64"),
+                                dict(nx=128, lattice="D2Q9", nz=1)])
+def test_pair_requested_on_ineligible_config_is_rejected(cm, kw):
+    args = dict(lattice="D3Q27", ny=4, nz=4, storage="f32", kernel="pair")
+    args.update(kw)
+    with pytest.raises(cm.CmlbmError) as e:
+        cm.Solver(**args)
+    assert e.value.code == cm.ERR_UNSUPPORTED
+
+
 @pytest.mark.parametrize("lattice,storage,tol", [("D3Q27", "f64", 1e-12), ("D3Q27", "f32", 2e-5), ("D2Q9", "f64", 1e-12)])
 def test_filtered_step_matches_oracle(cm, lattice, storage, tol):
     """Turbulence as forcing (Sec. 14): Smagorinsky closure force + factorized, reduced step."""

@@ -199,3 +199,28 @@ def test_slab_only_calls_are_rejected(cm):
         s.step_adjoint(s.get_state(), lam, lam.clone(), dF)
     assert e.value.code == cm.ERR_UNSUPPORTED
     s.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_slabs_with_the_two_cell_kernel(cm, storage):
+    """The packed two-cells-per-thread step on slabs against the same kernel on one domain."""
+    nx, ny, nz = 64, 6, 9
+    g = np.random.default_rng(11)
+    rho = 1.0 + 0.01 * g.standard_normal((nz, ny, nx))
+    u = 0.03 * g.standard_normal((3, nz, ny, nx))
+    kw = dict(lattice="D3Q27", nx=nx, ny=ny, storage=storage, tau=0.53, omega_bulk=1.0, smagorinsky_cs=0.1,
+              kernel="pair")
+    ref = cm.Solver(nz=nz, bc=("periodic", "bounceback", "periodic"), **kw)
+    ref.init(torch.tensor(rho, device="cuda"), torch.tensor(u, device="cuda"))
+    slabs = []
+    for r in range(2):
+        s, z0 = SL.cuda_slab(cm, nz, r, 2, bc=("periodic", "bounceback"), **kw)
+        sl = slice(z0, z0 + s.shape[0])
+        s.init(torch.tensor(rho[sl], device="cuda"), torch.tensor(u[:, sl], device="cuda"))
+        slabs.append(s)
+    ref.step(STEPS)
+    SL.SlabRun(slabs, SL.LocalExchange(slabs)).step(STEPS)
+    own = torch.cat([s.get_state()[:, 1:-1] for s in slabs], dim=1)
+    assert torch.equal(own.view(torch.uint8), ref.get_state().view(torch.uint8))
+    for s in slabs + [ref]:
+        s.close()
