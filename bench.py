@@ -28,6 +28,8 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 import torch  # noqa: E402
 
+# end-to-end job: upload (rho, u), initialise, E2E_STEPS steps, download (rho, u) and the sums
+E2E_STEPS = 50
 BYTES_PER_CELL = {("D3Q27", "f32"): 216, ("D3Q27", "bf16"): 108, ("D3Q27", "f16"): 108, ("D3Q27", "f64"): 432,
                   ("D2Q9", "f64"): 144, ("D2Q9", "f32"): 72}
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -41,7 +43,7 @@ OMEGA_BULK = 1.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=256, help="edge of the Taylor-Green box")
@@ -110,6 +112,11 @@ class Clocks:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            # nvidia-smi takes a moment to start: wait for its first sample so that the
+            # samples cover the timed region
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 3.0 and self.proc.poll() is None:
+                time.sleep(0.01)
         except (OSError, FileNotFoundError):
             self.proc = None
 
@@ -157,7 +164,8 @@ def peaks():
 
 # sources the direct D3Q27 step kernel is compiled from (and the flags it is built with)
 KERNEL_SOURCES = ("paper_1202_6074_gb300/csrc/cm_core.cuh", "paper_1202_6074_gb300/csrc/cm_kernels.cuh",
-                  "paper_1202_6074_gb300/csrc/cm_launch.h", "paper_1202_6074_gb300/csrc/inst_d3q27_f32.cu",
+                  "paper_1202_6074_gb300/csrc/cm_pair.cuh", "paper_1202_6074_gb300/csrc/cm_launch.h",
+                  "paper_1202_6074_gb300/csrc/inst_d3q27_f32.cu", "paper_1202_6074_gb300/csrc/inst_pair_f32.cu",
                   "paper_1202_6074_gb300/build.py")
 
 
@@ -383,7 +391,7 @@ def our_arm(args, dist):
     }
     if dist.rank == 0:
         torch.cuda.empty_cache()
-        line["e2e"] = e2e(cm, n, st, max(args.steps // 4, 10), kernel=args.kernel)
+        line["e2e"] = e2e(cm, n, st, E2E_STEPS, kernel=args.kernel)
         forms = {}
         if not args.no_forms:
             fs = args.form_steps

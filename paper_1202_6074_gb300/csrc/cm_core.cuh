@@ -127,9 +127,12 @@ template <class R> using scalar_t = typename Scalar<R>::T;
 
 // Compile-time features of a kernel variant: walls present, eddy viscosity, per-cell force
 // field, and the less common forms (factorized attractor / reduced compressibility) read from
-// Params at run time.
-template <bool WALLS_, bool LES_, bool FIELD_, bool GEN_> struct Feat {
-    static constexpr bool WALLS = WALLS_, LES = LES_, FIELD = FIELD_, GEN = GEN_;
+// Params at run time. SIMPLE: no force anywhere (sigma = 0 at every order) and
+// omega_3 = omega_4 = 1, so every moment of order >= 3 leaves the collision at its attractor
+// and the pre-collision moments of those orders are never needed (the compiler drops them).
+template <bool WALLS_, bool LES_, bool FIELD_, bool GEN_, bool SIMPLE_ = false> struct Feat {
+    static constexpr bool WALLS = WALLS_, LES = LES_, FIELD = FIELD_, GEN = GEN_, SIMPLE = SIMPLE_;
+    static_assert(!SIMPLE_ || (!FIELD_ && !GEN_), "SIMPLE excludes force fields and the general forms");
 };
 
 // ------------------------------------------------------------------------------------------
@@ -365,7 +368,7 @@ template <int D, class R> struct Hydro {
     R drho, jx, jy, jz, ux, uy, uz;
 };
 
-template <int D, class R, bool GEN = true>
+template <int D, class R, bool GEN = true, bool FORCED = true>
 __device__ __forceinline__ Hydro<D, R> hydro(const R (&h)[Lat<D>::Q], const R F[3], const PR<scalar_t<R>>& p) {
     constexpr int NL = Lat<D>::Q / 3;
     Hydro<D, R> o;
@@ -384,9 +387,15 @@ __device__ __forceinline__ Hydro<D, R> hydro(const R (&h)[Lat<D>::Q], const R F[
         for (int b = 0; b < 3; ++b) jz += s0[6 + b] - s0[b];
     }
     o.drho = drho;
-    o.jx = fma(R(0.5), F[0], jx);
-    o.jy = fma(R(0.5), F[1], jy);
-    o.jz = fma(R(0.5), F[2], jz);
+    if constexpr (FORCED) {
+        o.jx = fma(R(0.5), F[0], jx);
+        o.jy = fma(R(0.5), F[1], jy);
+        o.jz = fma(R(0.5), F[2], jz);
+    } else {
+        o.jx = jx;
+        o.jy = jy;
+        o.jz = jz;
+    }
     const R inv = rcp((GEN && p.reduced) ? R(p.rho0) : R(1) + drho);
     o.ux = o.jx * inv;
     o.uy = o.jy * inv;
@@ -466,7 +475,7 @@ template <int D, class R, class FT>
 __device__ __forceinline__ void collide(R (&m)[Lat<D>::Q], const R F[3], const PR<scalar_t<R>>& p, scalar_t<R> cs_eff) {
     using T = scalar_t<R>;
     constexpr int Q = Lat<D>::Q;
-    const Hydro<D, R> hy = hydro<D, R, FT::GEN>(m, F, p);
+    const Hydro<D, R> hy = hydro<D, R, FT::GEN, !FT::SIMPLE>(m, F, p);
     const R drho = hy.drho, rho = R(1) + hy.drho, ndrho = -hy.drho;
     const R u[3] = {hy.ux, hy.uy, hy.uz};
     central_forward<D, R>(m, u[0], u[1], u[2]);
@@ -537,50 +546,67 @@ __device__ __forceinline__ void collide(R (&m)[Lat<D>::Q], const R F[3], const P
     const R om3 = R(T(1) - p.omega3), om4 = R(T(1) - p.omega4);
     const bool factorized = FT::GEN && p.attractor != 0;
 
-    // orders >= 3 in increasing order: source by the hierarchical identity, attractor, relaxation
-    sfor<2 * D + 1>([&](auto NI) {
-        constexpr int n = decltype(NI)::value;
+    if constexpr (FT::SIMPLE) {
+        // no source and omega_3 = omega_4 = 1: orders >= 3 are set to their attractors
         sfor<Q>([&](auto TI) {
             constexpr int t = decltype(TI)::value;
-            if constexpr (n >= 3 && ord(t) == n) {
+            if constexpr (ord(t) >= 3) {
                 constexpr int a = ex_a(t), b = ex_b(t), c = ex_c(t);
-                R s = R(0);
-                if constexpr (a > 0) s = fma(a == 2 ? Fr2[0] : Fr[0], kap[t - 1], s);
-                if constexpr (b > 0) s = fma(b == 2 ? Fr2[1] : Fr[1], kap[t - 3], s);
-                if constexpr (c > 0) s = fma(c == 2 ? Fr2[2] : Fr[2], kap[t - 9], s);
-                const R hs = R(0.5) * s;
-                const R kw = weight_cm<R, a, b, c>(cw);
-                if constexpr (ord(t) < 2 * D) kap[t] = fma(R(0.5), s, m[t] + kw);
                 constexpr bool even = (a % 2 == 0) && (b % 2 == 0) && (c % 2 == 0);
-                constexpr int twos = (a == 2) + (b == 2) + (c == 2);
-                const R tp = R((T)third_pow(twos));
-                R DM;
-                if constexpr (even) DM = fma(drho, tp, -excess<R, a == 2, b == 2, c == 2>(q));
-                else DM = -kw;
-                if (factorized) {
-                    // Sec. 13: products of relaxed second-order moments / rho^(k-1)
-                    constexpr int ones = (a == 1) + (b == 1) + (c == 1);
-                    if constexpr (ones == 0) {
-                        const R pt[3] = {Txx * irho, Tyy * irho, Tzz * irho};
-                        R prodp = R(1);
-                        if constexpr (a == 2) prodp = prodp * (third + pt[0]);
-                        if constexpr (b == 2) prodp = prodp * (third + pt[1]);
-                        if constexpr (c == 2) prodp = prodp * (third + pt[2]);
-                        DM = fma(drho, prodp, excess<R, a == 2, b == 2, c == 2>(pt) - excess<R, a == 2, b == 2, c == 2>(q));
-                    } else if constexpr (ones == 2 && twos == 1) {
-                        constexpr int dtwo = (a == 2) ? 0 : (b == 2) ? 1 : 2;
-                        const R Tdg = dtwo == 0 ? Txx : dtwo == 1 ? Tyy : Tzz;
-                        const R Toff = (a != 1) ? Tyz : (b != 1) ? Txz : Txy;
-                        const R uoff = (a != 1) ? u[1] * u[2] : (b != 1) ? u[0] * u[2] : u[0] * u[1];
-                        DM = fma(Toff, fma(Tdg, irho, third), -((third + q[dtwo]) * uoff));
-                    }
+                if constexpr (even) {
+                    const R tp = R((T)third_pow((a == 2) + (b == 2) + (c == 2)));
+                    m[t] = fma(drho, tp, -excess<R, a == 2, b == 2, c == 2>(q));
+                } else {
+                    m[t] = -weight_cm<R, a, b, c>(cw);
                 }
-                const R w = (ord(t) == 3) ? w3 : w4;
-                const R om = (ord(t) == 3) ? om3 : om4;
-                m[t] = fma(om, m[t] + hs, fma(w, DM, hs));
             }
         });
-    });
+    } else {
+        // orders >= 3 in increasing order: source by the hierarchical identity, attractor, relaxation
+        sfor<2 * D + 1>([&](auto NI) {
+            constexpr int n = decltype(NI)::value;
+            sfor<Q>([&](auto TI) {
+                constexpr int t = decltype(TI)::value;
+                if constexpr (n >= 3 && ord(t) == n) {
+                    constexpr int a = ex_a(t), b = ex_b(t), c = ex_c(t);
+                    R s = R(0);
+                    if constexpr (a > 0) s = fma(a == 2 ? Fr2[0] : Fr[0], kap[t - 1], s);
+                    if constexpr (b > 0) s = fma(b == 2 ? Fr2[1] : Fr[1], kap[t - 3], s);
+                    if constexpr (c > 0) s = fma(c == 2 ? Fr2[2] : Fr[2], kap[t - 9], s);
+                    const R hs = R(0.5) * s;
+                    const R kw = weight_cm<R, a, b, c>(cw);
+                    if constexpr (ord(t) < 2 * D) kap[t] = fma(R(0.5), s, m[t] + kw);
+                    constexpr bool even = (a % 2 == 0) && (b % 2 == 0) && (c % 2 == 0);
+                    constexpr int twos = (a == 2) + (b == 2) + (c == 2);
+                    const R tp = R((T)third_pow(twos));
+                    R DM;
+                    if constexpr (even) DM = fma(drho, tp, -excess<R, a == 2, b == 2, c == 2>(q));
+                    else DM = -kw;
+                    if (factorized) {
+                        // Sec. 13: products of relaxed second-order moments / rho^(k-1)
+                        constexpr int ones = (a == 1) + (b == 1) + (c == 1);
+                        if constexpr (ones == 0) {
+                            const R pt[3] = {Txx * irho, Tyy * irho, Tzz * irho};
+                            R prodp = R(1);
+                            if constexpr (a == 2) prodp = prodp * (third + pt[0]);
+                            if constexpr (b == 2) prodp = prodp * (third + pt[1]);
+                            if constexpr (c == 2) prodp = prodp * (third + pt[2]);
+                            DM = fma(drho, prodp, excess<R, a == 2, b == 2, c == 2>(pt) - excess<R, a == 2, b == 2, c == 2>(q));
+                        } else if constexpr (ones == 2 && twos == 1) {
+                            constexpr int dtwo = (a == 2) ? 0 : (b == 2) ? 1 : 2;
+                            const R Tdg = dtwo == 0 ? Txx : dtwo == 1 ? Tyy : Tzz;
+                            const R Toff = (a != 1) ? Tyz : (b != 1) ? Txz : Txy;
+                            const R uoff = (a != 1) ? u[1] * u[2] : (b != 1) ? u[0] * u[2] : u[0] * u[1];
+                            DM = fma(Toff, fma(Tdg, irho, third), -((third + q[dtwo]) * uoff));
+                        }
+                    }
+                    const R w = (ord(t) == 3) ? w3 : w4;
+                    const R om = (ord(t) == 3) ? om3 : om4;
+                    m[t] = fma(om, m[t] + hs, fma(w, DM, hs));
+                }
+            });
+        });
+    }
 
     // second order back to deviations of the weights' moments
     m[midx(2, 0, 0)] = Txx + fma(drho, third, -q[0]);
@@ -592,9 +618,15 @@ __device__ __forceinline__ void collide(R (&m)[Lat<D>::Q], const R F[3], const P
         m[midx(0, 1, 1)] = fma(-u[1], u[2], Tyz);
     }
     // first order: collision invariant plus the source sigma_x = F_x
-    m[midx(1, 0, 0)] = fma(ndrho, u[0], fma(R(0.5), F[0], hy.jx));
-    m[midx(0, 1, 0)] = fma(ndrho, u[1], fma(R(0.5), F[1], hy.jy));
-    if constexpr (D == 3) m[midx(0, 0, 1)] = fma(ndrho, u[2], fma(R(0.5), F[2], hy.jz));
+    if constexpr (FT::SIMPLE) {
+        m[midx(1, 0, 0)] = fma(ndrho, u[0], hy.jx);
+        m[midx(0, 1, 0)] = fma(ndrho, u[1], hy.jy);
+        if constexpr (D == 3) m[midx(0, 0, 1)] = fma(ndrho, u[2], hy.jz);
+    } else {
+        m[midx(1, 0, 0)] = fma(ndrho, u[0], fma(R(0.5), F[0], hy.jx));
+        m[midx(0, 1, 0)] = fma(ndrho, u[1], fma(R(0.5), F[1], hy.jy));
+        if constexpr (D == 3) m[midx(0, 0, 1)] = fma(ndrho, u[2], fma(R(0.5), F[2], hy.jz));
+    }
     // zeroth order unchanged (m[0] = drho)
 
     central_inverse<D, R>(m, u[0], u[1], u[2]);

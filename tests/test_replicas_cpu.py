@@ -1,6 +1,6 @@
 """The N > 1 host path of bench.py on CPU: two gloo ranks, barrier and max-over-ranks timing.
 
-The step itself does not exchange data between GPUs (replicas only): each rank
+The benchmark runs the workload as replicas (no data exchange between GPUs): each rank
 runs the whole workload, so the only collectives are the barrier and the timing reduction.
 """
 import os
