@@ -321,6 +321,16 @@ def cpu_baseline(n=40, steps=4):
 # ------------------------------------------------------------------------------------------
 # arms
 # ------------------------------------------------------------------------------------------
+def workload_config(n, st, world):
+    """The benchmark's workload description (shared by both arms)."""
+    N = n ** 3
+    half = BYTES_PER_CELL[("D3Q27", st)] / 2 * N
+    return {"workload": f"D3Q27 CM-LBM {st.upper()} decaying Taylor-Green vortex {n}^3 periodic, u0=0.05, "
+                        f"Re=1600, no LES (tau={tgv_tau(n):.6f}, bulk rate {OMEGA_BULK})",
+            "cells": N, "l2": "state 2 x %.2f GB %s 129 MB L2, no flush" % (half / 1e9, ">>" if half > 129e6 else "vs"),
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def reference_arm(args, dist):
     """The oracle as it stands, timed on the host cores: each step = one oracle step on a 32^3
     Taylor-Green sample of the 256^3 workload."""
@@ -330,7 +340,9 @@ def reference_arm(args, dist):
     from oracle.collision import Params
     from paper_1202_6074_gb300 import workloads as W
 
-    n = 32
+    # sample edge sized so that warm-up + timed steps stay near a minute on the host cores
+    # (about 0.4 M cell updates/s): n^3 (steps + warmup) <= 24e6, 8 <= n <= 32
+    n = int(max(8, min(32, (24e6 / max(1, args.steps + args.warmup)) ** (1.0 / 3.0))))
     rho, u = W.taylor_green(n, n, n, u0=0.05)
     o = OracleSim("D3Q27", n, n, n, Params(tau=tgv_tau(args.n), omega_bulk=OMEGA_BULK))
     o.init(torch.tensor(rho), torch.tensor(u))
@@ -344,7 +356,7 @@ def reference_arm(args, dist):
         "impl": "reference", "metric": "MLUPS", "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * (t1 - t0) / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"D3Q27 Taylor-Green {args.n}^3 periodic, u0=0.05, Re=1600 (oracle sample {n}^3)"},
+        "config": workload_config(args.n, "f32", dist.world),
         "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": torch.get_num_threads(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -374,11 +386,7 @@ def our_arm(args, dist):
         "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": dist.world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": st, "data": "synthetic",
-        "config": {"workload": f"D3Q27 CM-LBM {st.upper()} decaying Taylor-Green vortex {n}^3 periodic, u0=0.05, "
-                               f"Re=1600, no LES (tau={tgv_tau(n):.6f}, bulk rate {OMEGA_BULK})",
-                   "cells": N, "l2": "state 2 x %.2f GB %s 129 MB L2, no flush" % (
-                       bpc / 2 * N / 1e9, ">>" if bpc / 2 * N > 129e6 else "vs"),
-                   "parallelism": "replicas" if dist.world > 1 else "single GPU"},
+        "config": workload_config(n, st, dist.world),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"], "peak_kind": pk_kind,
                      "traffic": None if traffic_pc is None else traffic_pc * N,

@@ -18,6 +18,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 
 #include "cm_kernels.cuh"
@@ -27,6 +28,7 @@ namespace cm {
 namespace {
 
 constexpr unsigned kWaitLimit = 1u << 22;     // try_wait rounds before a wait is declared stuck
+constexpr int kMaxTmaDevices = 64;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -245,11 +247,16 @@ cudaError_t launch_tma_ft(const void* map_main, const void* map_halo, const void
     if (((uintptr_t)src % 16) != 0 || ((size_t)p.nx * sizeof(S)) % 16 != 0 || (p.nx % TX) != 0)
         return cudaErrorMisalignedAddress;
     auto kern = k_step_tma<S, TX, STAGES, FT, HALO>;
-    static bool configured = false;
-    if (!configured) {
+    // the shared-memory opt-in is a per-device attribute of the kernel: set it once per device
+    static std::atomic<bool> configured[kMaxTmaDevices];
+    int dev = 0;
+    cudaError_t e0 = cudaGetDevice(&dev);
+    if (e0 != cudaSuccess) return e0;
+    if (dev < 0 || dev >= kMaxTmaDevices) return cudaErrorInvalidDevice;
+    if (!configured[dev].load()) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured[dev].store(true);
     }
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX + 32, smem);
