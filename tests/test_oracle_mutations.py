@@ -1,0 +1,127 @@
+"""The oracle's pins catch plausible mistakes: each test plants one mistake in the oracle (on the
+CPU, through monkeypatch) and runs the fast pin tests; at least one of them must fail.
+
+The mistakes are the ones a restatement of the paper could plausibly make: a dropped or
+sign-flipped F/2 in the velocity, a source without its sigma/2 feedback or with the wrong
+factor, a wrong Maxwellian moment, central moments about the wrong velocity, a transposed
+stream, swapped third/fourth-order rates, a wrong eddy-viscosity
+constant, a flipped moving-wall term, and an initial state without its -S/2 term.
+"""
+import inspect
+import os
+
+import pytest
+import torch
+
+import test_oracle_basis as TB
+import test_oracle_collision as TC
+import test_oracle_flows as TF
+import test_oracle_les as TL
+from oracle import collision as C
+from oracle import les as L
+from oracle import moments as M
+from oracle import stream as ST
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+SLOW = {"test_poiseuille_exact_with_magic_parameter", "test_poiseuille_default_rates_wall_error_is_small",
+        "test_couette_exact", "test_galilean_invariance_of_taylor_green_decay"}
+
+
+def _calls(module, include_slow=()):
+    """(name, thunk) for every test function of a module, expanded over its parametrizations."""
+    out = []
+    for name, fn in inspect.getmembers(module, inspect.isfunction):
+        if not name.startswith("test_") or (name in SLOW and name not in include_slow):
+            continue
+        params = [m for m in getattr(fn, "pytestmark", []) if m.name == "parametrize"]
+        sig = inspect.signature(fn).parameters
+        kw = {"golden_dir": GOLDEN} if "golden_dir" in sig else {}
+        combos = [dict(kw)]
+        for m in params:
+            names = [s.strip() for s in m.args[0].split(",")] if isinstance(m.args[0], str) else list(m.args[0])
+            new = []
+            for c in combos:
+                for v in m.args[1]:
+                    vals = v if len(names) > 1 else (v,)
+                    d = dict(c)
+                    d.update(zip(names, vals))
+                    new.append(d)
+            combos = new
+        for c in combos:
+            out.append((f"{module.__name__}::{name}{c}", (lambda f=fn, c=c: f(**c))))
+    return out
+
+
+def _failures(include_slow=()):
+    failed = []
+    for mod in (TB, TC, TF, TL):
+        for name, thunk in _calls(mod, include_slow):
+            try:
+                thunk()
+            except Exception:  # noqa: BLE001  (a pin that fails, however it fails)
+                failed.append(name)
+    return failed
+
+
+def test_the_pins_pass_without_a_mistake():
+    assert _failures() == []
+
+
+def _wrap(monkeypatch, module, name, make):
+    orig = getattr(module, name)
+    monkeypatch.setattr(module, name, make(orig))
+
+
+def _source_without_feedback(kbar, rho, F, lat):
+    """The hierarchical identity applied to kbar instead of kappa = kbar + sigma/2."""
+    idx = {a: k for k, a in enumerate(lat.monomials)}
+    sigma, kappa = [None] * len(idx), [None] * len(idx)
+    for a in lat.monomials:
+        k = idx[a]
+        s = torch.zeros_like(rho)
+        for d in range(3):
+            if a[d] > 0:
+                lower = list(a)
+                lower[d] -= 1
+                s = s + a[d] * (F[d] / rho) * kappa[idx[tuple(lower)]]
+        sigma[k] = s
+        n = sum(a)
+        kappa[k] = rho if n == 0 else torch.zeros_like(rho) if n == 1 else kbar[k]
+    return torch.stack(sigma), torch.stack(kappa)
+
+
+MUTATIONS = {
+    "velocity without F/2": lambda mp: _wrap(mp, C, "hydrodynamics",
+                                             lambda f: lambda fbar, F, lat, p=None: f(fbar, 0 * F, lat, p)),
+    "velocity with -F/2": lambda mp: _wrap(mp, C, "hydrodynamics",
+                                           lambda f: lambda fbar, F, lat, p=None: f(fbar, -F, lat, p)),
+    "source doubled": lambda mp: _wrap(mp, C, "source_central",
+                                       lambda f: lambda kbar, rho, F, lat: (lambda s, k: (2 * s, k))(*f(kbar, rho, F, lat))),
+    "source without sigma/2 feedback": lambda mp: mp.setattr(C, "source_central", _source_without_feedback),
+    "fourth-order Maxwellian moment off": lambda mp: _wrap(
+        mp, C, "maxwell_central",
+        lambda f: lambda rho, lat: f(rho, lat) * torch.tensor(
+            [1.05 if sum(a) == 4 else 1.0 for a in lat.monomials], dtype=rho.dtype).view(-1, *([1] * rho.dim()))),
+    "central moments about -u": lambda mp: _wrap(mp, M, "central_moments", lambda f: lambda g, u, lat: f(g, -u, lat)),
+    "stream transposed": lambda mp: mp.setattr(ST, "pull", lambda s, lat, bc, uw, _u=ST.unstream: _u(s, lat, bc, uw)),
+    "third and fourth rates swapped": lambda mp: _wrap(
+        mp, C, "collide",
+        lambda f: lambda fbar, F, lat, p, cs_eff=None: f(fbar, F, lat, type(p)(**{**p.__dict__, "omega3": p.omega4,
+                                                                                 "omega4": p.omega3}), cs_eff)),
+    "eddy viscosity constant 18 instead of 18 sqrt 2": lambda mp: _wrap(
+        mp, L, "tau_effective",
+        lambda f: lambda tau0, cs, Pi, rho: f(tau0, cs / 2 ** 0.25, Pi, rho)),
+    "moving-wall term flipped": lambda mp: _wrap(
+        mp, ST, "_wall_terms",
+        lambda f: lambda lat, i, shape, bc, uw, sign: (lambda m, w: (m, -w))(*f(lat, i, shape, bc, uw, sign))),
+    "initial state without -S/2": lambda mp: _wrap(mp, C, "equilibrium", lambda f: lambda rho, u, F, lat: f(rho, u, 0 * F, lat)),
+}
+
+
+@pytest.mark.parametrize("name", list(MUTATIONS))
+def test_a_planted_mistake_fails_a_pin(monkeypatch, name):
+    MUTATIONS[name](monkeypatch)
+    failed = _failures()
+    if not failed:      # the slow closed-form flows are the last line
+        failed = _failures(include_slow=SLOW)
+    assert failed, f"no pin catches: {name}"
