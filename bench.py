@@ -238,6 +238,22 @@ def run_tgv(cm, n, storage, steps, warmup, dist, clocks=None, kernel="auto"):
     return ms, launches, ck, red, kernel_used
 
 
+def run_poiseuille(cm, steps=5000):
+    """The D2Q9 FP64 body-force channel, 64 x 32, 5000 steps (2048 cells: launch bound; the
+    library replays pairs of steps as CUDA graphs)."""
+    stream = torch.cuda.current_stream()
+    s = cm.Solver(lattice="D2Q9", nx=64, ny=32, nz=1, storage="f64", tau=0.8,
+                  bc=("periodic", "bounceback", "periodic"))
+    s.set_force((1e-6, 0.0, 0.0))
+    s.init()
+    ms, launches = time_steps(s, steps, 10, Dist0(), stream)
+    red = s.reduce()
+    s.close()
+    sec = ms / 1e3
+    return {"MLUPS": 64 * 32 * steps / sec / 1e6, "us_per_step": 1e6 * sec / steps, "steps": steps,
+            "launches": int(launches), "mean_ux": red[1] / red[0]}
+
+
 def run_hit_les(cm, n, storage, steps, warmup, dist):
     from paper_1202_6074_gb300 import workloads as W
 
@@ -428,6 +444,10 @@ def our_arm(args, dist):
             except Exception as e:  # noqa: BLE001
                 forms["channel1024x256x256_les_bf16"] = {"error": str(e)[:200]}
             torch.cuda.empty_cache()
+            try:
+                forms["d2q9_poiseuille64x32_f64"] = run_poiseuille(cm)
+            except Exception as e:  # noqa: BLE001
+                forms["d2q9_poiseuille64x32_f64"] = {"error": str(e)[:200]}
             try:
                 from paper_1202_6074_gb300 import rollout
 

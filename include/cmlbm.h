@@ -163,7 +163,11 @@ CMLBM_API int cmlbm_set_force(cmlbm_t* h, const double uniform[3], const double*
  * on `where`; rho NULL means 1, u NULL means 0. The step counter is reset. */
 CMLBM_API int cmlbm_init(cmlbm_t* h, const double* rho, const double* u, int where);
 
-/* Advance nsteps stream-and-collide steps (nsteps >= 0). */
+/* Advance nsteps stream-and-collide steps (nsteps >= 0): the pull of Eq. cascadedstreaming1
+ * followed by the collision of Sec. 10, fused in one kernel launch per step, asynchronous on the
+ * handle's stream. Pairs of steps are replayed as a CUDA graph (captured once per buffer parity
+ * on a private stream, dropped when the force changes), so a call of many steps costs one graph
+ * launch per two steps; a failed capture falls back to plain launches for the handle's life. */
 CMLBM_API int cmlbm_step(cmlbm_t* h, int nsteps);
 
 /* One step from the state buffer src into dst (device pointers, Q*N storage elements each,

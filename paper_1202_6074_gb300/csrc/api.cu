@@ -35,6 +35,16 @@ struct cmlbm {
     int nsm = 0;
     void* turb = nullptr;      // [10][N] arithmetic type: rho, u, eddy stress (turbulence forcing)
     size_t ghost = 0;          // elements before the first own plane of a state buffer (nx ny on a slab)
+    // CUDA graphs of two consecutive steps (state in buf[k] -> buf[1-k] -> buf[k]), one per
+    // starting buffer, captured on a private stream and replayed on `st` by cmlbm_step; dropped
+    // whenever the parameters or the force buffer change
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+#ifdef CM_NO_GRAPHS
+    bool graphs = false;       // build option: plain launches only
+#else
+    bool graphs = true;        // false after a capture failed: plain launches from then on
+#endif
 };
 
 namespace {
@@ -123,6 +133,40 @@ cudaError_t do_step(cmlbm* h, const void* src, void* dst) {
         using S = std::remove_pointer_t<decltype(s)>;
         return cm::launch_step<decltype(d)::value, S>(own(h, src), own(h, dst), h->force, h->p, h->st);
     });
+}
+
+void drop_graphs(cmlbm* h) {
+    for (int k = 0; k < 2; ++k) {
+        if (h->gexec[k]) cudaGraphExecDestroy(h->gexec[k]);
+        h->gexec[k] = nullptr;
+    }
+}
+
+// Capture the two steps buf[k] -> buf[1-k] -> buf[k] into an executable graph. Any failure
+// leaves no capture open and returns the error (the caller then launches plainly).
+cudaError_t capture_two_steps(cmlbm* h, int k, cudaGraphExec_t* out) {
+    if (!h->cap) {
+        cudaError_t e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+    }
+    cudaStream_t saved = h->st;
+    const long long launches = h->launches;
+    h->st = h->cap;
+    cudaError_t e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
+    cudaError_t e1 = cudaSuccess, e2 = cudaSuccess;
+    if (e == cudaSuccess) {
+        e1 = do_step(h, h->buf[k], h->buf[1 - k]);
+        e2 = do_step(h, h->buf[1 - k], h->buf[k]);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t ee = (e == cudaSuccess) ? cudaStreamEndCapture(h->cap, &graph) : e;
+    h->st = saved;
+    h->launches = launches;
+    if (e1 == cudaSuccess) e1 = e2;
+    if (e1 == cudaSuccess) e1 = ee;
+    if (e1 == cudaSuccess) e1 = cudaGraphInstantiate(out, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    return e1;
 }
 
 cudaError_t do_moments(cmlbm* h, const void* src, double* rho, double* u) {
@@ -300,6 +344,8 @@ void cmlbm_destroy(cmlbm_t* h) {
     if (!h) return;
     DeviceGuard g(h->cfg.device);
     cudaStreamSynchronize(h->st);
+    drop_graphs(h);
+    if (h->cap) cudaStreamDestroy(h->cap);
     cudaFree(h->buf[0]);
     cudaFree(h->buf[1]);
     cudaFree(h->force);
@@ -330,6 +376,7 @@ size_t cmlbm_state_bytes(const cmlbm_t* h) { return h ? (size_t)h->Q * (size_t)h
 int cmlbm_set_force(cmlbm_t* h, const double uniform[3], const double* field, int where) {
     if (!h) return CMLBM_ERR_INVALID;
     DeviceGuard g(h->cfg.device);
+    drop_graphs(h);            // the captured steps carry the old force parameters
     for (int d = 0; d < 3; ++d) {
         const double v = uniform ? uniform[d] : 0.0;
         if (!std::isfinite(v)) return fail(h, CMLBM_ERR_INVALID, "uniform force must be finite");
@@ -407,6 +454,21 @@ int cmlbm_step(cmlbm_t* h, int nsteps) {
     if (!h) return CMLBM_ERR_INVALID;
     if (nsteps < 0) return fail(h, CMLBM_ERR_INVALID, "nsteps must be >= 0");
     DeviceGuard g(h->cfg.device);
+    // pairs of steps as graph replays (one graph launch instead of two kernel launches)
+    if (nsteps >= 2 && h->graphs && !h->tma) {
+        if (!h->gexec[h->cur] && capture_two_steps(h, h->cur, &h->gexec[h->cur]) != cudaSuccess) {
+            cudaGetLastError();
+            h->gexec[h->cur] = nullptr;
+            h->graphs = false;
+        }
+        if (h->gexec[h->cur]) {
+            for (; nsteps >= 2; nsteps -= 2) {
+                cudaError_t e = cudaGraphLaunch(h->gexec[h->cur], h->st);
+                if (e != cudaSuccess) return cuda_fail(h, e, "step graph launch");
+                h->launches += 2;
+            }
+        }
+    }
     for (int k = 0; k < nsteps; ++k) {
         cudaError_t e = do_step(h, h->buf[h->cur], h->buf[1 - h->cur]);
         if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
@@ -512,6 +574,7 @@ int cmlbm_turbulence_force(cmlbm_t* h, double cs) {
         return fail(h, CMLBM_ERR_UNSUPPORTED, "turbulence forcing needs periodic boundaries");
     DeviceGuard g(h->cfg.device);
     const size_t N = (size_t)h->p.N;
+    if (!h->force || !h->p.has_field) drop_graphs(h);   // the steps will read a (new) force field
     if (!h->force && cudaMalloc(&h->force, h->rsize * 3 * N) != cudaSuccess) {
         h->force = nullptr;
         cudaGetLastError();

@@ -507,3 +507,27 @@ def test_filtered_step_rejects_walls(cm):
         s.turbulence_force(0.1)
     assert e.value.code == cm.ERR_UNSUPPORTED
     s.close()
+
+
+@pytest.mark.parametrize("kernel", ["pair", "direct"])
+def test_graph_replayed_steps_equal_single_steps(cm, kernel):
+    """cmlbm_step replays pairs of steps as a CUDA graph; the result must equal one-by-one steps,
+    also across a force change (the captured parameters are dropped) and odd step counts."""
+    case = PAIR_CASES["pair_walls_les_vd"]
+    rho, u, F = _inputs(case)
+    a, _ = _pair(cm, case["lattice"], case["shape"], "f32", rho, u, F, kernel=kernel, **case["kw"])
+    b, _ = _pair(cm, case["lattice"], case["shape"], "f32", rho, u, F, kernel=kernel, **case["kw"])
+    la, lb = a.launch_count, b.launch_count
+    a.step(7)
+    for _ in range(7):
+        b.step(1)
+    assert torch.equal(a.get_state(), b.get_state())
+    a.set_force((3e-5, 0.0, -1e-5))
+    b.set_force((3e-5, 0.0, -1e-5))
+    a.step(6)
+    for _ in range(6):
+        b.step(1)
+    assert torch.equal(a.get_state(), b.get_state())
+    assert a.launch_count - la == b.launch_count - lb == 13
+    a.close()
+    b.close()
