@@ -254,6 +254,60 @@ def run_poiseuille(cm, steps=5000):
             "launches": int(launches), "mean_ux": red[1] / red[0]}
 
 
+def _events_ms(fn, stream):
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b)
+
+
+def run_filtered(cm, n, steps):
+    """Turbulence as forcing (the filtered equation) on the Taylor-Green flow: every step
+    recomputes the closure force (three kernels) and then steps; FP32, n^3 periodic, factorized
+    attractor and reduced compressibility as for the filtered form."""
+    from paper_1202_6074_gb300 import workloads as W
+
+    stream = torch.cuda.current_stream()
+    s = cm.Solver(lattice="D3Q27", nx=n, ny=n, nz=n, storage="f32", tau=0.5005, omega_bulk=OMEGA_BULK,
+                  attractor="factorized", reduced_compressibility=True)
+    rho, u = W.taylor_green(n, n, n, u0=0.05, xp=torch, device="cuda")
+    s.init(rho, u)
+    del rho, u
+    s.step_filtered(3, 0.1)
+    l0 = s.launch_count
+    ms = _events_ms(lambda: s.step_filtered(steps, 0.1), stream)
+    launches = s.launch_count - l0
+    s.close()
+    return {"MLUPS": n ** 3 * steps / (ms / 1e3) / 1e6, "steps": steps, "launches_per_step": launches / steps}
+
+
+def run_slabs(cm, n, k, steps):
+    """The Taylor-Green workload split into k z-slabs on this GPU, faces exchanged every step
+    (in-process exchange): the cost of the decomposition against one domain."""
+    from paper_1202_6074_gb300 import slab as SL, workloads as W
+
+    stream = torch.cuda.current_stream()
+    rho, u = W.taylor_green(n, n, n, u0=0.05, xp=torch, device="cuda")
+    slabs = []
+    for r in range(k):
+        s, z0 = SL.cuda_slab(cm, n, r, k, lattice="D3Q27", nx=n, ny=n, storage="f32", tau=tgv_tau(n),
+                             omega_bulk=OMEGA_BULK)
+        s.init(rho[z0:z0 + s.shape[0]].contiguous(), u[:, z0:z0 + s.shape[0]].contiguous())
+        slabs.append(s)
+    del rho, u
+    run = SL.SlabRun(slabs, SL.LocalExchange(slabs))
+    run.step(3)
+    ms = _events_ms(lambda: run.step(steps), stream)
+    red = run.reduce()
+    for s in slabs:
+        s.close()
+    return {"MLUPS": n ** 3 * steps / (ms / 1e3) / 1e6, "slabs": k, "steps": steps, "mass": red[0]}
+
+
 def run_hit_les(cm, n, storage, steps, warmup, dist):
     from paper_1202_6074_gb300 import workloads as W
 
@@ -443,6 +497,16 @@ def our_arm(args, dist):
                                                          / pk["hbm_gbs"], "steps": fs}
             except Exception as e:  # noqa: BLE001
                 forms["channel1024x256x256_les_bf16"] = {"error": str(e)[:200]}
+            torch.cuda.empty_cache()
+            try:
+                forms["filtered_hit256_f32"] = run_filtered(cm, 256, fs)
+            except Exception as e:  # noqa: BLE001
+                forms["filtered_hit256_f32"] = {"error": str(e)[:200]}
+            try:
+                forms["slabs2_tgv256_f32"] = run_slabs(cm, n, 2, fs)
+            except Exception as e:  # noqa: BLE001
+                forms["slabs2_tgv256_f32"] = {"error": str(e)[:200]}
+            torch.cuda.empty_cache()
             torch.cuda.empty_cache()
             try:
                 forms["d2q9_poiseuille64x32_f64"] = run_poiseuille(cm)

@@ -403,6 +403,57 @@ __device__ __forceinline__ Hydro<D, R> hydro(const R (&h)[Lat<D>::Q], const R F[
     return o;
 }
 
+// The collision's first pass over the populations: the raw moments of every x-line (three
+// populations with e_x = -1, 0, +1): (sum, sum e_x, sum e_x^2), in place. The hydrodynamic
+// fields are sums of these, and the x-sweep of the central transform continues from them.
+template <int D, class R> __device__ __forceinline__ void raw_x(R (&m)[Lat<D>::Q]) {
+    constexpr int NL = Lat<D>::Q / 3;
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+        const R a = m[3 * l], b = m[3 * l + 1], c = m[3 * l + 2];
+        const R s1 = c - a, s2 = c + a;
+        m[3 * l] = s2 + b;
+        m[3 * l + 1] = s1;
+        m[3 * l + 2] = s2;
+    }
+}
+
+// rho - 1 and the momentum (Eqs. densitycalculation, velocitycalculation) from the raw x-line
+// moments: line l = (e_y + 1) + 3 (e_z + 1)
+template <int D, class R, bool GEN = true, bool FORCED = true>
+__device__ __forceinline__ Hydro<D, R> hydro_x(const R (&m)[Lat<D>::Q], const R F[3], const PR<scalar_t<R>>& p) {
+    constexpr int NL = Lat<D>::Q / 3;
+    Hydro<D, R> o;
+    R drho = m[0], jx = m[1];
+#pragma unroll
+    for (int l = 1; l < NL; ++l) {
+        drho += m[3 * l];
+        jx += m[3 * l + 1];
+    }
+    R jy = R(0), jz = R(0);
+#pragma unroll
+    for (int c = 0; c < NL / 3; ++c) jy += m[3 * (3 * c + 2)] - m[3 * (3 * c)];
+    if constexpr (D == 3) {
+#pragma unroll
+        for (int b = 0; b < 3; ++b) jz += m[3 * (6 + b)] - m[3 * b];
+    }
+    o.drho = drho;
+    if constexpr (FORCED) {
+        o.jx = fma(R(0.5), F[0], jx);
+        o.jy = fma(R(0.5), F[1], jy);
+        o.jz = fma(R(0.5), F[2], jz);
+    } else {
+        o.jx = jx;
+        o.jy = jy;
+        o.jz = jz;
+    }
+    const R inv = rcp((GEN && p.reduced) ? R(p.rho0) : R(1) + drho);
+    o.ux = o.jx * inv;
+    o.uy = o.jy * inv;
+    o.uz = (D == 3) ? o.jz * inv : R(0);
+    return o;
+}
+
 // Forward sweeps: deviation populations (slot order) -> central moments of h about u.
 template <int D, class R>
 __device__ __forceinline__ void central_forward(R (&m)[Lat<D>::Q], R ux, R uy, R uz) {
@@ -411,6 +462,30 @@ __device__ __forceinline__ void central_forward(R (&m)[Lat<D>::Q], R ux, R uy, R
     const R tx = nx + nx, ty = ny + ny, tz = nz + nz, qx = ux * ux, qy = uy * uy, qz = uz * uz;
 #pragma unroll
     for (int l = 0; l < NL; ++l) fwd1(m[3 * l], m[3 * l + 1], m[3 * l + 2], nx, tx, qx);
+#pragma unroll
+    for (int c = 0; c < Lat<D>::NZ; ++c)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) fwd1(m[9 * c + a], m[9 * c + 3 + a], m[9 * c + 6 + a], ny, ty, qy);
+    if constexpr (D == 3) {
+#pragma unroll
+        for (int t = 0; t < 9; ++t) fwd1(m[t], m[9 + t], m[18 + t], nz, tz, qz);
+    }
+}
+
+// The forward transform continued from the raw x-line moments of raw_x(): shift the x-moments
+// to central ones about u_x, (m0, s1, s2) -> (m0, s1 - u m0, s2 - 2u s1 + u^2 m0), then the
+// y and z sweeps. Equal to central_forward() on the populations.
+template <int D, class R>
+__device__ __forceinline__ void central_forward_from_x(R (&m)[Lat<D>::Q], R ux, R uy, R uz) {
+    constexpr int NL = Lat<D>::Q / 3;
+    const R nx = -ux, ny = -uy, nz = -uz;
+    const R tx = nx + nx, ty = ny + ny, tz = nz + nz, qx = ux * ux, qy = uy * uy, qz = uz * uz;
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+        const R m0 = m[3 * l], s1 = m[3 * l + 1], s2 = m[3 * l + 2];
+        m[3 * l + 1] = fma(nx, m0, s1);
+        m[3 * l + 2] = fma(qx, m0, fma(tx, s1, s2));
+    }
 #pragma unroll
     for (int c = 0; c < Lat<D>::NZ; ++c)
 #pragma unroll
@@ -475,10 +550,11 @@ template <int D, class R, class FT>
 __device__ __forceinline__ void collide(R (&m)[Lat<D>::Q], const R F[3], const PR<scalar_t<R>>& p, scalar_t<R> cs_eff) {
     using T = scalar_t<R>;
     constexpr int Q = Lat<D>::Q;
-    const Hydro<D, R> hy = hydro<D, R, FT::GEN, !FT::SIMPLE>(m, F, p);
+    raw_x<D, R>(m);
+    const Hydro<D, R> hy = hydro_x<D, R, FT::GEN, !FT::SIMPLE>(m, F, p);
     const R drho = hy.drho, rho = R(1) + hy.drho, ndrho = -hy.drho;
     const R u[3] = {hy.ux, hy.uy, hy.uz};
-    central_forward<D, R>(m, u[0], u[1], u[2]);
+    central_forward_from_x<D, R>(m, u[0], u[1], u[2]);
 
     const R third = R(T(1) / 3);
     const R q[3] = {u[0] * u[0], u[1] * u[1], u[2] * u[2]};
