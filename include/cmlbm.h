@@ -136,10 +136,11 @@ typedef struct {
  * no eddy viscosity, Maxwellian attractor, rho0 = 1, default stream, device 0. */
 CMLBM_API int cmlbm_config_default(cmlbm_config* cfg);
 
-/* Validate cfg, allocate two state buffers of Q*N storage elements on cfg->device and
+/* Validate cfg, allocate two state buffers of cmlbm_state_bytes() each on cfg->device and
  * initialise the rest state (rho = 1, u = 0, F = 0). *out receives the handle.
  * Errors: CMLBM_ERR_INVALID (bad sizes, tau <= 1/2, D2Q9 with nz != 1, van Driest without
- * y walls), CMLBM_ERR_NOMEM, CMLBM_ERR_CUDA. On error *out is NULL. */
+ * y walls, an unknown kernel), CMLBM_ERR_UNSUPPORTED (an explicit kernel choice the
+ * configuration cannot use), CMLBM_ERR_NOMEM, CMLBM_ERR_CUDA. On error *out is NULL. */
 CMLBM_API int cmlbm_create(const cmlbm_config* cfg, cmlbm_t** out);
 
 /* Release all device memory of the handle. NULL-safe. Synchronises the handle's stream. */
@@ -160,7 +161,7 @@ CMLBM_API int cmlbm_set_force(cmlbm_t* h, const double uniform[3], const double*
 /* Initialise the state so that the next pull returns fbar = f^M(rho, u) - S/2 with the
  * current force, S evaluated at the Maxwellian moments (paper silent on initialisation;
  * the special case noted under Eq. exactidentitycomponents). rho [N] and u [3][N] are FP64
- * on `where`; rho NULL means 1, u NULL means 0. The step counter is reset. */
+ * on `where`; rho NULL means 1, u NULL means 0. */
 CMLBM_API int cmlbm_init(cmlbm_t* h, const double* rho, const double* u, int where);
 
 /* Advance nsteps stream-and-collide steps (nsteps >= 0): the pull of Eq. cascadedstreaming1
@@ -170,9 +171,9 @@ CMLBM_API int cmlbm_init(cmlbm_t* h, const double* rho, const double* u, int whe
  * launch per two steps; a failed capture falls back to plain launches for the handle's life. */
 CMLBM_API int cmlbm_step(cmlbm_t* h, int nsteps);
 
-/* One step from the state buffer src into dst (device pointers, Q*N storage elements each,
- * not the handle's own buffers, src != dst), with the handle's configuration and force.
- * Used for checkpointed recomputation; the handle's own state is untouched. */
+/* One step from the state buffer src into dst (device pointers of cmlbm_state_bytes() each,
+ * in the handle's layout, src != dst), with the handle's configuration and force. Used for
+ * checkpointed recomputation; the handle's own state is untouched. */
 CMLBM_API int cmlbm_step_buffers(cmlbm_t* h, const void* src, void* dst);
 
 /* Density [N] and velocity [3][N] (FP64) of the current pre-collision field (pull of the
