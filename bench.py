@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--form-steps", type=int, default=40)
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"],
                     help="population storage of the timed Taylor-Green step (f32 is the headline)")
-    ap.add_argument("--kernel", default="auto", choices=["auto", "direct", "pair", "tma"],
+    ap.add_argument("--kernel", default="auto", choices=["auto", "direct", "pair", "pair_two_steps", "tma"],
                     help="step kernel: the library's choice (auto), one cell per thread (direct), two cells "
                          "per thread in packed FP32 (pair), or rows staged by TMA (tma)")
     return ap.parse_args()
@@ -342,9 +342,12 @@ def run_channel(cm, storage, steps, warmup, dist, nx=1024, ny=256, nz=256):
     return ms, launches
 
 
-def e2e(cm, n, storage, steps, kernel="auto"):
+def e2e(cm, n, storage, steps, kernel="auto", repeats=3):
     """Whole job through the C ABI with host buffers: upload (rho, u) from pinned memory, init,
-    `steps` steps, download (rho, u) and the FP64 reductions; wall clock around all of it."""
+    `steps` steps, download (rho, u) and the FP64 reductions; wall clock around all of it. The
+    job is repeated `repeats` times (a new handle each time) and the median run is reported: the
+    host link is shared with the machine's other GPUs, and a download occasionally stalls for
+    tens of ms (every run is listed)."""
     from paper_1202_6074_gb300 import workloads as W
 
     rho, u = W.taylor_green(n, n, n, u0=0.05, xp=torch, device="cuda")
@@ -353,22 +356,32 @@ def e2e(cm, n, storage, steps, kernel="auto"):
     del rho, u
     rho_o = torch.empty_like(rho_h).pin_memory()
     u_o = torch.empty_like(u_h).pin_memory()
-    s = cm.Solver(lattice="D3Q27", nx=n, ny=n, nz=n, storage=storage, tau=tgv_tau(n), omega_bulk=OMEGA_BULK,
-                  kernel=kernel)
-    lib = s.lib
-    P = cm._ptr
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    s._check(lib.cmlbm_init(s.h, P(rho_h), P(u_h), cm.HOST))
-    s.step(steps)
-    s._check(lib.cmlbm_moments(s.h, P(rho_o), P(u_o), cm.HOST))
-    red = s.reduce()
-    t1 = time.perf_counter()
-    s.close()
     N = n ** 3
-    assert math.isfinite(red[0])
-    return {"value": N * steps / (t1 - t0) / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": 32 * N / steps,
-            "d2h_bytes_per_step": (32 * N + 40) / steps, "steps": steps}
+    runs = []
+    for _ in range(repeats):
+        s = cm.Solver(lattice="D3Q27", nx=n, ny=n, nz=n, storage=storage, tau=tgv_tau(n), omega_bulk=OMEGA_BULK,
+                      kernel=kernel)
+        lib = s.lib
+        P = cm._ptr
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s._check(lib.cmlbm_init(s.h, P(rho_h), P(u_h), cm.HOST))
+        ta = time.perf_counter()
+        s.step(steps)
+        s._check(lib.cmlbm_moments(s.h, P(rho_o), P(u_o), cm.HOST))
+        tb = time.perf_counter()
+        red = s.reduce()
+        t1 = time.perf_counter()
+        s.close()
+        assert math.isfinite(red[0])
+        # wall-clock split: upload + init, steps + moments download (the steps run asynchronously
+        # until the download waits for them), reduction
+        runs.append((N * steps / (t1 - t0) / 1e6,
+                     {"init": 1e3 * (ta - t0), "steps_and_moments": 1e3 * (tb - ta), "reduce": 1e3 * (t1 - tb)}))
+    best = sorted(runs, key=lambda r: r[0])[len(runs) // 2]
+    return {"value": best[0], "unit": "MLUPS", "h2d_bytes_per_step": 32 * N / steps,
+            "d2h_bytes_per_step": (32 * N + 40) / steps, "steps": steps, "split_ms": best[1],
+            "runs_MLUPS": [r[0] for r in runs]}
 
 
 def cpu_baseline(n=40, steps=4):
@@ -461,7 +474,8 @@ def our_arm(args, dist):
                      "frac": achieved / pk["hbm_gbs"], "peak_kind": pk_kind,
                      "traffic": None if traffic_pc is None else traffic_pc * N,
                      "algorithmic_bytes_per_cell": bpc,
-                     "kernel": {"tma": "k_step_tma", "pair": "k_step_pair", "direct": "k_step"}[kname]
+                     "kernel": {"tma": "k_step_tma", "pair": "k_step_pair", "direct": "k_step",
+                                "pair_two_steps": "k_step_pair (two steps per pass)"}[kname]
                                + f"<D3Q27,{st},periodic>"},
         "clocks": ck,
         "gpu_launches": int(launches),

@@ -65,7 +65,8 @@ enum { CMLBM_F64 = 0, CMLBM_F32 = 1, CMLBM_BF16 = 2, CMLBM_F16 = 3 }; /* state s
 enum { CMLBM_PERIODIC = 0, CMLBM_BOUNCEBACK = 1, CMLBM_HALO = 2 };  /* per-axis boundary */
 enum { CMLBM_DEVICE = 0, CMLBM_HOST = 1 };                         /* where a buffer lives */
 enum { CMLBM_ATTRACTOR_MAXWELL = 0, CMLBM_ATTRACTOR_FACTORIZED = 1 };
-enum { CMLBM_KERNEL_AUTO = 0, CMLBM_KERNEL_DIRECT = 1, CMLBM_KERNEL_TMA = 2, CMLBM_KERNEL_PAIR = 3 };
+enum { CMLBM_KERNEL_AUTO = 0, CMLBM_KERNEL_DIRECT = 1, CMLBM_KERNEL_TMA = 2, CMLBM_KERNEL_PAIR = 3,
+       CMLBM_KERNEL_PAIR_TWO_STEPS = 4 };
 
 typedef struct cmlbm cmlbm_t;
 
@@ -100,11 +101,15 @@ typedef struct cmlbm cmlbm_t;
  *   rho0                  reference density of the reduced-compressibility form.
  *   stream                cudaStream_t to launch on; NULL = the legacy default stream.
  *   device                CUDA device ordinal the handle lives on.
- *   kernel                step kernel: CMLBM_KERNEL_AUTO (the two-cells-per-thread kernel where
- *                         the configuration allows it, else one cell per thread: the fastest
- *                         measured), CMLBM_KERNEL_DIRECT (one cell per thread),
+ *   kernel                step kernel: CMLBM_KERNEL_AUTO (the fastest measured that the
+ *                         configuration allows: two cells per thread, else one cell per
+ *                         thread), CMLBM_KERNEL_DIRECT (one cell per thread),
  *                         CMLBM_KERNEL_PAIR (two cells of a row per thread in packed FP32
- *                         arithmetic), or CMLBM_KERNEL_TMA (rows staged in shared memory by TMA).
+ *                         arithmetic), CMLBM_KERNEL_PAIR_TWO_STEPS (the PAIR kernel scheduled two
+ *                         steps per pass: z-planes in groups of 8, the intermediate state in a
+ *                         ring of 12 planes meant to stay in L2; FP32 storage, no slab,
+ *                         nz >= 16; bitwise the same results, measured slower than PAIR on
+ *                         GB300), or CMLBM_KERNEL_TMA (rows staged in shared memory by TMA).
  *                         PAIR covers D3Q27 with FP32 / BF16 / FP16 storage, periodic x, nx a
  *                         multiple of 64, the Maxwellian attractor and standard compressibility;
  *                         TMA covers D3Q27 with FP32 / BF16 / FP16 storage, nx a multiple of 128,
@@ -267,8 +272,9 @@ CMLBM_API int cmlbm_halo_unpack(cmlbm_t* h, int face, const void* in, int where)
 /* Kernel launches issued by the handle so far (for benchmark accounting). */
 CMLBM_API long long cmlbm_launch_count(const cmlbm_t* h);
 
-/* The step kernel the handle runs: CMLBM_KERNEL_DIRECT, CMLBM_KERNEL_PAIR or CMLBM_KERNEL_TMA
- * (what CMLBM_KERNEL_AUTO resolved to); CMLBM_ERR_INVALID for a NULL handle. */
+/* The step kernel the handle runs: CMLBM_KERNEL_DIRECT, CMLBM_KERNEL_PAIR,
+ * CMLBM_KERNEL_PAIR_TWO_STEPS or CMLBM_KERNEL_TMA (what CMLBM_KERNEL_AUTO resolved to);
+ * CMLBM_ERR_INVALID for a NULL handle. */
 CMLBM_API int cmlbm_step_kernel(const cmlbm_t* h);
 
 /* ---- allocation-free reduction (no counterpart in the paper) --------------------------- *

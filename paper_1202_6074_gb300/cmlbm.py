@@ -32,7 +32,7 @@ SYMBOLS = ["cmlbm_config_default", "cmlbm_create", "cmlbm_destroy", "cmlbm_last_
            "cmlbm_adjoint_terminal", "cmlbm_step_adjoint", "cmlbm_launch_count", "cmlbm_reduce_noalloc",
            "cmlbm_turbulence_force", "cmlbm_step_filtered", "cmlbm_halo_bytes", "cmlbm_halo_pack",
            "cmlbm_halo_unpack", "cmlbm_step_kernel"]
-KERNELS = {0: "auto", 1: "direct", 2: "tma", 3: "pair"}
+KERNELS = {0: "auto", 1: "direct", 2: "tma", 3: "pair", 4: "pair_two_steps"}
 
 
 class Config(ctypes.Structure):
@@ -156,7 +156,8 @@ def make_config(lattice="D3Q27", nx=32, ny=32, nz=32, storage="f32", bc=("period
     c.rho0 = float(rho0)
     c.device = int(device)
     c.stream = stream
-    c.kernel = {"auto": 0, "direct": 1, "tma": 2, "pair": 3}[kernel] if isinstance(kernel, str) else int(kernel)
+    c.kernel = ({"auto": 0, "direct": 1, "tma": 2, "pair": 3, "pair_two_steps": 4}[kernel] if isinstance(kernel, str)
+                else int(kernel))
     return c
 
 

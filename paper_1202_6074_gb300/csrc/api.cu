@@ -40,6 +40,10 @@ struct cmlbm {
     // whenever the parameters or the force buffer change
     cudaStream_t cap = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    // two steps per pass: the plane ring of the intermediate state (allocated on first use)
+    bool two_steps = false;
+    void* ring = nullptr;
+    int pass_launches = 0;     // kernel launches of one two-step pass
 #ifdef CM_NO_GRAPHS
     bool graphs = false;       // build option: plain launches only
 #else
@@ -142,8 +146,24 @@ void drop_graphs(cmlbm* h) {
     }
 }
 
-// Capture the two steps buf[k] -> buf[1-k] -> buf[k] into an executable graph. Any failure
-// leaves no capture open and returns the error (the caller then launches plainly).
+// Enqueue two steps from buf[k]: buf[k] -> buf[1-k] -> buf[k] as two single steps, or, on a
+// two-steps handle, one pass buf[k] -> buf[1-k] through the plane ring (the state then ends in
+// buf[1-k]).
+cudaError_t enqueue_two_steps(cmlbm* h, int k) {
+    if (h->two_steps) {
+        const int n = cm::launch_two_steps_f32(h->buf[k], h->buf[1 - k], h->ring, h->force, h->p, h->st);
+        if (n < 0) return cudaErrorInvalidValue;
+        h->pass_launches = n;
+        h->launches += n;
+        return cudaSuccess;
+    }
+    cudaError_t e = do_step(h, h->buf[k], h->buf[1 - k]);
+    if (e == cudaSuccess) e = do_step(h, h->buf[1 - k], h->buf[k]);
+    return e;
+}
+
+// Capture the two steps from buf[k] into an executable graph. Any failure leaves no capture
+// open and returns the error (the caller then launches plainly).
 cudaError_t capture_two_steps(cmlbm* h, int k, cudaGraphExec_t* out) {
     if (!h->cap) {
         cudaError_t e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
@@ -154,10 +174,7 @@ cudaError_t capture_two_steps(cmlbm* h, int k, cudaGraphExec_t* out) {
     h->st = h->cap;
     cudaError_t e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
     cudaError_t e1 = cudaSuccess, e2 = cudaSuccess;
-    if (e == cudaSuccess) {
-        e1 = do_step(h, h->buf[k], h->buf[1 - k]);
-        e2 = do_step(h, h->buf[1 - k], h->buf[k]);
-    }
+    if (e == cudaSuccess) e1 = enqueue_two_steps(h, k);
     cudaGraph_t graph = nullptr;
     cudaError_t ee = (e == cudaSuccess) ? cudaStreamEndCapture(h->cap, &graph) : e;
     h->st = saved;
@@ -169,11 +186,12 @@ cudaError_t capture_two_steps(cmlbm* h, int k, cudaGraphExec_t* out) {
     return e1;
 }
 
-cudaError_t do_moments(cmlbm* h, const void* src, double* rho, double* u) {
+cudaError_t do_moments(cmlbm* h, const void* src, double* rho, double* u, int z0 = 0, int nzc = -1) {
     ++h->launches;
     return dispatch(h, [&](auto d, auto* s) {
         using S = std::remove_pointer_t<decltype(s)>;
-        return cm::launch_moments<decltype(d)::value, S>(own(h, src), h->force, h->p, rho, u, h->st);
+        return cm::launch_moments<decltype(d)::value, S>(own(h, src), h->force, h->p, rho, u, h->st, z0,
+                                                         nzc < 0 ? h->p.nz : nzc);
     });
 }
 
@@ -228,7 +246,8 @@ int cmlbm_create(const cmlbm_config* cfg, cmlbm_t** out) {
         if (c.bc[a] != CMLBM_PERIODIC && c.bc[a] != CMLBM_BOUNCEBACK && !(a == 2 && c.bc[a] == CMLBM_HALO))
             return fail(nullptr, CMLBM_ERR_INVALID,
                         "bc must be CMLBM_PERIODIC or CMLBM_BOUNCEBACK (or CMLBM_HALO on z)");
-    if (c.kernel < CMLBM_KERNEL_AUTO || c.kernel > CMLBM_KERNEL_PAIR) return fail(nullptr, CMLBM_ERR_INVALID, "unknown kernel");
+    if (c.kernel < CMLBM_KERNEL_AUTO || c.kernel > CMLBM_KERNEL_PAIR_TWO_STEPS)
+        return fail(nullptr, CMLBM_ERR_INVALID, "unknown kernel");
     const bool slab = c.bc[2] == CMLBM_HALO;
     if (slab && c.lattice != CMLBM_D3Q27) return fail(nullptr, CMLBM_ERR_INVALID, "CMLBM_HALO needs D3Q27");
     const long long S = slab ? (long long)c.nx * c.ny * (c.nz + 2) : N;
@@ -303,6 +322,18 @@ int cmlbm_create(const cmlbm_config* cfg, cmlbm_t** out) {
     }
     if (cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess) h->nsm = 1;
     if (c.kernel == CMLBM_KERNEL_AUTO && cm::pair_eligible(p, h->D, c.storage != CMLBM_F64)) p.pair = 1;
+    const bool two_ok = cm::two_steps_eligible(p, h->D, c.storage == CMLBM_F32, slab);
+    if (c.kernel == CMLBM_KERNEL_PAIR_TWO_STEPS && !two_ok) {
+        cmlbm_destroy(h);
+        return fail(nullptr, CMLBM_ERR_UNSUPPORTED,
+                    "two steps per pass need D3Q27, FP32 storage, periodic x, nx a multiple of 64, nz >= 16, "
+                    "no slab and the standard collision");
+    }
+    // opt-in only: measured slower than single steps of the pair kernel (see the header)
+    if (c.kernel == CMLBM_KERNEL_PAIR_TWO_STEPS && two_ok) {
+        p.pair = 1;
+        h->two_steps = true;
+    }
     if (c.kernel == CMLBM_KERNEL_PAIR) {
         if (!cm::pair_eligible(p, h->D, c.storage != CMLBM_F64)) {
             cmlbm_destroy(h);
@@ -354,6 +385,7 @@ void cmlbm_destroy(cmlbm_t* h) {
     cudaFree(h->stage);
     cudaFree(h->flag);
     cudaFree(h->turb);
+    cudaFree(h->ring);
     delete h;
 }
 
@@ -368,6 +400,7 @@ long long cmlbm_launch_count(const cmlbm_t* h) { return h ? h->launches : 0; }
 int cmlbm_step_kernel(const cmlbm_t* h) {
     if (!h) return CMLBM_ERR_INVALID;
     if (h->tma) return CMLBM_KERNEL_TMA;
+    if (h->two_steps) return CMLBM_KERNEL_PAIR_TWO_STEPS;
     return h->p.pair ? CMLBM_KERNEL_PAIR : CMLBM_KERNEL_DIRECT;
 }
 
@@ -419,6 +452,14 @@ int cmlbm_init(cmlbm_t* h, const double* rho, const double* u, int where) {
     if (where != CMLBM_DEVICE && where != CMLBM_HOST) return fail(h, CMLBM_ERR_INVALID, "bad `where`");
     DeviceGuard g(h->cfg.device);
     const size_t N = (size_t)h->p.N;
+    void* dst = own(h, h->buf[h->cur]);
+    auto launch = [&](const double* r, const double* v, int z0, int nzc) {
+        ++h->launches;
+        return dispatch(h, [&](auto d, auto* s) {
+            using S = std::remove_pointer_t<decltype(s)>;
+            return cm::launch_init<decltype(d)::value, S>(dst, h->force, h->p, r, v, h->st, z0, nzc);
+        });
+    };
     const double* drho = rho;
     const double* du = u;
     if (where == CMLBM_HOST && (rho || u)) {
@@ -435,13 +476,7 @@ int cmlbm_init(cmlbm_t* h, const double* rho, const double* u, int where) {
             du = h->stage + N;
         }
     }
-    void* tmp = own(h, h->buf[1 - h->cur]);
-    void* dst = own(h, h->buf[h->cur]);
-    h->launches += 2;
-    cudaError_t e = dispatch(h, [&](auto d, auto* s) {
-        using S = std::remove_pointer_t<decltype(s)>;
-        return cm::launch_init<decltype(d)::value, S>(tmp, dst, h->force, h->p, drho, du, h->st);
-    });
+    cudaError_t e = launch(drho, du, 0, h->p.nz);
     if (e != cudaSuccess) return cuda_fail(h, e, "init kernels");
     if (where == CMLBM_HOST) {
         e = cudaStreamSynchronize(h->st);
@@ -454,20 +489,42 @@ int cmlbm_step(cmlbm_t* h, int nsteps) {
     if (!h) return CMLBM_ERR_INVALID;
     if (nsteps < 0) return fail(h, CMLBM_ERR_INVALID, "nsteps must be >= 0");
     DeviceGuard g(h->cfg.device);
-    // pairs of steps as graph replays (one graph launch instead of two kernel launches)
+    if (nsteps >= 2 && h->two_steps && !h->ring) {
+        const size_t bytes = (size_t)(cm::kTwoStepRing + 2) * h->p.nx * h->p.ny * h->Q * h->esize;
+        if (cudaMalloc(&h->ring, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            h->ring = nullptr;
+            h->two_steps = false;      // no room for the ring: single steps
+            drop_graphs(h);
+        }
+    }
+    // pairs of steps as graph replays (one graph launch instead of two or more kernel launches)
     if (nsteps >= 2 && h->graphs && !h->tma) {
         if (!h->gexec[h->cur] && capture_two_steps(h, h->cur, &h->gexec[h->cur]) != cudaSuccess) {
             cudaGetLastError();
             h->gexec[h->cur] = nullptr;
             h->graphs = false;
         }
-        if (h->gexec[h->cur]) {
-            for (; nsteps >= 2; nsteps -= 2) {
-                cudaError_t e = cudaGraphLaunch(h->gexec[h->cur], h->st);
-                if (e != cudaSuccess) return cuda_fail(h, e, "step graph launch");
+        for (; nsteps >= 2 && h->gexec[h->cur]; nsteps -= 2) {
+            cudaError_t e = cudaGraphLaunch(h->gexec[h->cur], h->st);
+            if (e != cudaSuccess) return cuda_fail(h, e, "step graph launch");
+            if (h->two_steps) {
+                h->launches += h->pass_launches;
+                h->cur ^= 1;
+                if (nsteps >= 4 && !h->gexec[h->cur] && capture_two_steps(h, h->cur, &h->gexec[h->cur]) != cudaSuccess) {
+                    cudaGetLastError();
+                    h->gexec[h->cur] = nullptr;
+                }
+            } else {
                 h->launches += 2;
             }
         }
+    }
+    // without graphs: two-step passes launched directly
+    for (; nsteps >= 2 && h->two_steps; nsteps -= 2) {
+        cudaError_t e = enqueue_two_steps(h, h->cur);
+        if (e != cudaSuccess) return cuda_fail(h, e, "two-step pass");
+        h->cur ^= 1;
     }
     for (int k = 0; k < nsteps; ++k) {
         cudaError_t e = do_step(h, h->buf[h->cur], h->buf[1 - h->cur]);

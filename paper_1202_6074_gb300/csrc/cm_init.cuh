@@ -6,16 +6,26 @@
 
 namespace cm {
 
-// ---- equilibrium at the cell -----------------------------------------------------------------
+// ---- one pass: equilibrium at the cell, written where the first pull reads it --------------
+// Each cell x computes its pre-collision field fbar = f^M - S/2 (deviation d = fbar/w - 1) and
+// writes direction j where the first pull will read it: s_j(x - e_j) = d_j(x), or, when x - e_j
+// is behind a wall, the entry the bounce-back reads, s_jbar(x) = d_j(x) - 6 (e_j . u_w) (u_w
+// the mean velocity of the walls crossed; side 0 is below index 0, side 1 above n - 1). Every
+// state entry that a pull reads is written by exactly one cell: the cell that pulls it.
+// On a slab (bc[2] == 2) the entries pulled across a face land in the ghost planes (z = -1, nz);
+// the entries of the own planes that only a neighbour pulls are left unwritten (the neighbour
+// holds the same values in its ghost plane). Offsets are 32-bit unsigned: a ghost row below
+// has a negative row offset only for e_z = +1 (directions 18..26), so every final offset is
+// in [0, Q*S).
 template <int D, class S>
-__global__ void __launch_bounds__(kBlock) k_equilibrium(S* __restrict__ dst, const typename Codec<S>::R* __restrict__ Ff,
-                                                       PR<typename Codec<S>::R> p, const double* __restrict__ rho,
-                                                       const double* __restrict__ u) {
+__global__ void __launch_bounds__(kBlock) k_init(S* __restrict__ dst, const typename Codec<S>::R* __restrict__ Ff,
+                                                PR<typename Codec<S>::R> p, const double* __restrict__ rho,
+                                                const double* __restrict__ u, int z0) {
     using R = typename Codec<S>::R;
     constexpr int Q = Lat<D>::Q;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
+    const int z = (int)blockIdx.z + z0;
     if (x >= p.nx || y >= p.ny) return;
     const unsigned cell = (unsigned)((z * p.ny + y) * p.nx + x);
     R F[3];
@@ -29,39 +39,13 @@ __global__ void __launch_bounds__(kBlock) k_equilibrium(S* __restrict__ dst, con
     }
     R m[Q];
     equilibrium<D, R>(m, (R)r, (R)ux, (R)uy, (R)uz, F);
-    sfor<Q>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        constexpr R iw = (R)inv_weight<D>(i);
-        Codec<S>::st(dst + ((unsigned)i * p.S + cell), m[slot<D>(i)] * iw);
-    });
-}
 
-// ---- inverse of the pull -----------------------------------------------------------------------
-// s_i(x) = fbar_i(x + e_i), or, when x + e_i is behind a wall, the value whose bounce-back gives
-// fbar_{ibar}(x): fbar_{ibar}(x) + 6 w_i (e_i . u_w) in deviation form d (the mean u_w of the
-// walls crossed). The three shifted coordinates per axis are formed once, and the 27 (9)
-// directions are unrolled at compile time like the pull itself.
-// On a slab (bc[2] == 2) the grid's z index also covers the two ghost planes (z = -1 and nz):
-// an entry whose x + e_i lies outside the slab's own planes is left unwritten (this slab never
-// pulls it; the neighbour holds the same value in its ghost plane), and a reflected entry is
-// written only for the slab's own cells (it is pulled by its own cell).
-// Offsets are 32-bit unsigned: every offset written or read is in [0, Q*S) even where a ghost
-// row's part of it is negative (ghost entries below exist only for e_z = +1, i >= 18).
-template <int D, class S>
-__global__ void __launch_bounds__(kBlock) k_unstream(const S* __restrict__ fb, S* __restrict__ dst, PR<typename Codec<S>::R> p) {
-    using R = typename Codec<S>::R;
-    const bool slab = p.bc[2] == 2;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = (int)blockIdx.z - (slab ? 1 : 0);
-    if (x >= p.nx || y >= p.ny) return;
-    const bool ghost = z < 0 || z >= p.nz;
+    // target coordinate x - e per axis for slot k <-> e = k - 1, and whether a wall is crossed
     int tx[3], ty[3], tz[3];
     bool wx[3] = {false, false, false}, wy[3] = {false, false, false}, wz[3] = {false, false, false};
-    bool beyond[3] = {false, false, false};
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {          // slot k <-> e = k - 1, target coordinate = x + e
-        int sx = x + k - 1, sy = y + k - 1, sz = z + k - 1;
+    for (int k = 0; k < 3; ++k) {
+        int sx = x + 1 - k, sy = y + 1 - k, sz = z + 1 - k;
         if (sx < 0 || sx >= p.nx) {
             if (p.bc[0] != 1) sx += (sx < 0) ? p.nx : -p.nx;
             else { wx[k] = true; sx = x; }
@@ -73,8 +57,8 @@ __global__ void __launch_bounds__(kBlock) k_unstream(const S* __restrict__ fb, S
         if (D == 3) {
             if (sz < 0 || sz >= p.nz) {
                 if (p.bc[2] == 0) sz += (sz < 0) ? p.nz : -p.nz;
-                else if (p.bc[2] == 2) beyond[k] = true;
-                else { wz[k] = true; sz = z; }
+                else if (p.bc[2] == 1) { wz[k] = true; sz = z; }
+                // bc[2] == 2 (slab): the ghost plane at -1 or nz
             }
         } else {
             sz = 0;
@@ -83,41 +67,40 @@ __global__ void __launch_bounds__(kBlock) k_unstream(const S* __restrict__ fb, S
         ty[k] = sy;
         tz[k] = sz;
     }
-    const unsigned cell = (unsigned)((z * p.ny + y) * p.nx + x);
     const unsigned PS = p.S;
-    sfor<Lat<D>::Q>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        constexpr int a = Lat<D>::ex(i) + 1, b = Lat<D>::ey(i) + 1, c = Lat<D>::ez(i) + 1;
+    sfor<Q>([&](auto I) {
+        constexpr int j = decltype(I)::value;
+        constexpr int a = Lat<D>::ex(j) + 1, b = Lat<D>::ey(j) + 1, c = Lat<D>::ez(j) + 1;
+        constexpr R iw = (R)inv_weight<D>(j);
+        const R d = m[slot<D>(j)] * iw;
         const bool out = wx[a] || wy[b] || wz[c];
-        if (out ? ghost : beyond[c]) return;
-        R d;
         if (out) {
-            // the walls crossed on the way to x + e_i; side 0 below index 0, side 1 above n - 1
-            constexpr int sx = (a == 0) ? 0 : 1, sy = (b == 0) ? 0 : 1, sz = (c == 0) ? 0 : 1;
-            constexpr R ex = (R)Lat<D>::ex(i), ey = (R)Lat<D>::ey(i), ez = (R)Lat<D>::ez(i);
+            // the walls crossed going from x to x - e_j: e = +1 crosses the lower wall (side 0)
+            constexpr int sx = (a == 2) ? 0 : 1, sy = (b == 2) ? 0 : 1, sz = (c == 2) ? 0 : 1;
+            constexpr R ex = (R)Lat<D>::ex(j), ey = (R)Lat<D>::ey(j), ez = (R)Lat<D>::ez(j);
             R eu = R(0);
             if (wx[a]) eu += ex * p.uw[0][sx][0] + ey * p.uw[0][sx][1] + ez * p.uw[0][sx][2];
             if (wy[b]) eu += ex * p.uw[1][sy][0] + ey * p.uw[1][sy][1] + ez * p.uw[1][sy][2];
             if (wz[c]) eu += ex * p.uw[2][sz][0] + ey * p.uw[2][sz][1] + ez * p.uw[2][sz][2];
             const int cnt = (int)wx[a] + (int)wy[b] + (int)wz[c];
-            d = Codec<S>::ld(fb + (Lat<D>::opp(i) * PS + cell)) + R(6) * eu / R(cnt);
+            Codec<S>::st(dst + (Lat<D>::opp(j) * PS + cell), d - R(6) * eu / R(cnt));
         } else {
             const unsigned t = (unsigned)((tz[c] * p.ny + ty[b]) * p.nx + tx[a]);
-            d = Codec<S>::ld(fb + (i * PS + t));
+            Codec<S>::st(dst + (j * PS + t), d);
         }
-        Codec<S>::st(dst + (i * PS + cell), d);
     });
 }
 
+// the cells of the z-planes z0 .. z0 + nzc - 1 (their writes may land in neighbouring planes:
+// every entry has exactly one writer, so chunks of planes may run in any order)
 template <int D, class S>
-cudaError_t launch_init(void* tmp, void* dst, const void* Ff, const Params& p, const double* rho, const double* u,
-                        cudaStream_t st) {
+cudaError_t launch_init(void* dst, const void* Ff, const Params& p, const double* rho, const double* u, cudaStream_t st,
+                        int z0, int nzc) {
     using R = typename Codec<S>::R;
-    const dim3 b = cell_block(p.nx), g = cell_grid(p, b);
-    k_equilibrium<D, S><<<g, b, 0, st>>>((S*)tmp, (const R*)Ff, typed<R>(p), rho, u);
-    dim3 gu = g;
-    if (p.bc[2] == 2) gu.z += 2;      // slab: the ghost planes receive the entries leaving the slab
-    k_unstream<D, S><<<gu, b, 0, st>>>((const S*)tmp, (S*)dst, typed<R>(p));
+    const dim3 b = cell_block(p.nx);
+    dim3 g = cell_grid(p, b);
+    g.z = nzc;
+    k_init<D, S><<<g, b, 0, st>>>((S*)dst, (const R*)Ff, typed<R>(p), rho, u, z0);
     return cudaGetLastError();
 }
 

@@ -85,11 +85,12 @@ void launch_pair(const void* src, void* dst, const void* Ff, const Params& p, cu
 // ---- density and velocity of the pulled field ----------------------------------------------
 template <int D, class S, bool WALLS>
 __global__ void __launch_bounds__(kBlock) k_moments(const S* __restrict__ src, const typename Codec<S>::R* __restrict__ Ff,
-                                                   PR<typename Codec<S>::R> p, double* __restrict__ rho, double* __restrict__ u) {
+                                                   PR<typename Codec<S>::R> p, double* __restrict__ rho, double* __restrict__ u,
+                                                   int z0) {
     using R = typename Codec<S>::R;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
+    const int z = (int)blockIdx.z + z0;
     if (x >= p.nx || y >= p.ny) return;
     const unsigned cell = (unsigned)((z * p.ny + y) * p.nx + x);
     R h[Lat<D>::Q];
@@ -251,13 +252,16 @@ cudaError_t launch_step(const void* src, void* dst, const void* Ff, const Params
 }
 
 template <int D, class S>
-cudaError_t launch_moments(const void* src, const void* Ff, const Params& p, double* rho, double* u, cudaStream_t st) {
+cudaError_t launch_moments(const void* src, const void* Ff, const Params& p, double* rho, double* u, cudaStream_t st,
+                           int z0, int nzc) {
     using R = typename Codec<S>::R;
-    const dim3 b = cell_block(p.nx), g = cell_grid(p, b);
+    const dim3 b = cell_block(p.nx);
+    dim3 g = cell_grid(p, b);
+    g.z = nzc;
     if (has_walls(p))
-        k_moments<D, S, true><<<g, b, 0, st>>>((const S*)src, (const R*)Ff, typed<R>(p), rho, u);
+        k_moments<D, S, true><<<g, b, 0, st>>>((const S*)src, (const R*)Ff, typed<R>(p), rho, u, z0);
     else
-        k_moments<D, S, false><<<g, b, 0, st>>>((const S*)src, (const R*)Ff, typed<R>(p), rho, u);
+        k_moments<D, S, false><<<g, b, 0, st>>>((const S*)src, (const R*)Ff, typed<R>(p), rho, u, z0);
     return cudaGetLastError();
 }
 
@@ -286,8 +290,8 @@ cudaError_t launch_reduce(const void* src, const void* Ff, const Params& p, doub
 #define CM_INSTANTIATE(D, S)                                                                               \
     template cudaError_t cm::launch_step<D, S>(const void*, void*, const void*, const cm::Params&, cudaStream_t); \
     template cudaError_t cm::launch_moments<D, S>(const void*, const void*, const cm::Params&, double*, double*, \
-                                                  cudaStream_t);                                           \
-    template cudaError_t cm::launch_init<D, S>(void*, void*, const void*, const cm::Params&, const double*,  \
-                                               const double*, cudaStream_t);                               \
+                                                  cudaStream_t, int, int);                                 \
+    template cudaError_t cm::launch_init<D, S>(void*, const void*, const cm::Params&, const double*,         \
+                                               const double*, cudaStream_t, int, int);                     \
     template cudaError_t cm::launch_reduce<D, S>(const void*, const void*, const cm::Params&, double*, double*, \
                                                  cudaStream_t);

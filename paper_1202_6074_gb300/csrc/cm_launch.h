@@ -10,11 +10,13 @@
 namespace cm {
 template <int D, class S>
 cudaError_t launch_step(const void* src, void* dst, const void* Ff, const Params& p, cudaStream_t st);
+// moments and the initial state of the z-planes z0 .. z0 + nzc - 1
 template <int D, class S>
-cudaError_t launch_moments(const void* src, const void* Ff, const Params& p, double* rho, double* u, cudaStream_t st);
+cudaError_t launch_moments(const void* src, const void* Ff, const Params& p, double* rho, double* u, cudaStream_t st,
+                           int z0, int nzc);
 template <int D, class S>
-cudaError_t launch_init(void* tmp, void* dst, const void* Ff, const Params& p, const double* rho, const double* u,
-                        cudaStream_t st);
+cudaError_t launch_init(void* dst, const void* Ff, const Params& p, const double* rho, const double* u, cudaStream_t st,
+                        int z0, int nzc);
 template <int D, class S>
 cudaError_t launch_reduce(const void* src, const void* Ff, const Params& p, double* part, double* out, cudaStream_t st);
 cudaError_t launch_convert_force(const double* in, void* out, long long n, bool fp64, cudaStream_t st);
@@ -35,6 +37,16 @@ constexpr int kReduceMaxBlocks = 1216;
 inline bool pair_eligible(const Params& p, int D, bool fp32_arith) {
     return D == 3 && fp32_arith && p.bc[0] == 0 && p.nx % 64 == 0 && p.attractor == 0 && !p.reduced;
 }
+
+// Two steps per pass for FP32 storage (launch_pair_two_steps, inst_pair_tb_f32.cu): planes in
+// groups of kTwoStepGroup, the intermediate state in a ring of kTwoStepRing + 2 planes.
+constexpr int kTwoStepGroup = 8;
+constexpr int kTwoStepRing = kTwoStepGroup + 2;     // the planes a group's second step reads
+inline bool two_steps_eligible(const Params& p, int D, int storage_f32, bool slab) {
+    return storage_f32 && !slab && pair_eligible(p, D, true) && p.nz >= 2 * kTwoStepGroup;
+}
+// enqueue one pass (steps t -> t+2) from A into C; returns the number of kernel launches or -1
+int launch_two_steps_f32(const void* A, void* C, void* ring, const void* Ff, const Params& p, cudaStream_t st);
 
 // turbulence as forcing (turbulence.cu): scratch holds 10 N arithmetic values
 template <int D, class S>

@@ -11,9 +11,26 @@ namespace cm {
 #ifndef CM_PAIR_MIN_BLOCKS
 #define CM_PAIR_MIN_BLOCKS 4
 #endif
-template <class S, bool WALLS>
-__device__ __forceinline__ void gather_pair(const S* __restrict__ src, int x, int y, int z, const PR<float>& p, F2 (&h)[27]) {
-    const unsigned PS = p.S;
+
+// Plane ring of the two-steps-per-pass schedule (launch_pair_two_steps): the intermediate state
+// t+1 lives in a small buffer of z-planes instead of a full state buffer. Plane z sits in slot
+// z for z < 2 (kept until the end of the pass: the periodic wrap reads them last) and in slot
+// 2 + (z - 2) mod slots otherwise; direction planes are `stride` elements apart.
+struct Ring {
+    unsigned stride;       // elements between direction planes of the ring buffer
+    unsigned nxy;          // elements of one z-plane
+    int slots;             // ring slots after the two kept planes
+    int z0;                // first plane of the launch (blockIdx.z counts from it)
+    __device__ __forceinline__ unsigned plane(int z) const {
+        return (unsigned)(z < 2 ? z : 2 + (z - 2) % slots) * nxy;
+    }
+};
+
+// RS / RD: the source / destination state is the ring (else a full buffer with stride p.S)
+template <class S, bool WALLS, bool RS = false>
+__device__ __forceinline__ void gather_pair(const S* __restrict__ src, int x, int y, int z, const PR<float>& p, F2 (&h)[27],
+                                            const Ring& ring = Ring{}) {
+    const unsigned PS = RS ? ring.stride : p.S;
     const int half = p.nx >> 1;
     int xa[3], xb[3], ys[3], zs[3];
     bool yo[3] = {false, false, false}, zo[3] = {false, false, false};
@@ -36,12 +53,24 @@ __device__ __forceinline__ void gather_pair(const S* __restrict__ src, int x, in
         ys[k] = sy;
         zs[k] = sz;
     }
-    const unsigned cellA = (unsigned)((z * p.ny + y) * p.nx + x), cellB = cellA + (unsigned)half;
+    unsigned cellA, cellB;        // own cells in the source buffer
     unsigned row[3][3];
+    if constexpr (RS) {
+        cellA = ring.plane(z) + (unsigned)(y * p.nx + x);
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
+        for (int c = 0; c < 3; ++c) {
+            const unsigned pl = ring.plane(zs[c]);
 #pragma unroll
-        for (int b = 0; b < 3; ++b) row[c][b] = (unsigned)((zs[c] * p.ny + ys[b]) * p.nx);
+            for (int b = 0; b < 3; ++b) row[c][b] = pl + (unsigned)(ys[b] * p.nx);
+        }
+    } else {
+        cellA = (unsigned)((z * p.ny + y) * p.nx + x);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) row[c][b] = (unsigned)((zs[c] * p.ny + ys[b]) * p.nx);
+    }
+    cellB = cellA + (unsigned)half;
     sfor<27>([&](auto I) {
         constexpr int i = decltype(I)::value;
         constexpr int a = Lat<3>::ex(i) + 1, b = Lat<3>::ey(i) + 1, c = Lat<3>::ez(i) + 1;
@@ -66,23 +95,26 @@ __device__ __forceinline__ void gather_pair(const S* __restrict__ src, int x, in
     });
 }
 
-template <class S, class FT>
+template <class S, class FT, bool RS = false, bool RD = false>
 __global__ void __launch_bounds__(kBlock, CM_PAIR_MIN_BLOCKS) k_step_pair(const S* __restrict__ src, S* __restrict__ dst,
-                                                                          const float* __restrict__ Ff, PR<float> p) {
+                                                                          const float* __restrict__ Ff, PR<float> p,
+                                                                          Ring ring) {
     const int half = p.nx >> 1;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
+    const int z = (RS || RD) ? (int)blockIdx.z + ring.z0 : (int)blockIdx.z;
     if (x >= half || y >= p.ny) return;
+    // global cells (force field) and the destination cells
     const unsigned cellA = (unsigned)((z * p.ny + y) * p.nx + x), cellB = cellA + (unsigned)half;
-    const unsigned PS = p.S;
+    const unsigned dA = RD ? ring.plane(z) + (unsigned)(y * p.nx + x) : cellA, dB = dA + (unsigned)half;
+    const unsigned PS = RD ? ring.stride : p.S;
     F2 h[27];
     if constexpr (FT::WALLS) {
         const bool near = (p.bc[1] == 1 && (y == 0 || y == p.ny - 1)) || (p.bc[2] == 1 && (z == 0 || z == p.nz - 1));
-        if (near) gather_pair<S, true>(src, x, y, z, p, h);
-        else gather_pair<S, false>(src, x, y, z, p, h);
+        if (near) gather_pair<S, true, RS>(src, x, y, z, p, h, ring);
+        else gather_pair<S, false, RS>(src, x, y, z, p, h, ring);
     } else {
-        gather_pair<S, false>(src, x, y, z, p, h);
+        gather_pair<S, false, RS>(src, x, y, z, p, h, ring);
     }
     F2 F[3];
     if (FT::FIELD && p.has_field) {
@@ -98,8 +130,8 @@ __global__ void __launch_bounds__(kBlock, CM_PAIR_MIN_BLOCKS) k_step_pair(const 
         constexpr int i = decltype(I)::value;
         constexpr float iw = (float)inv_weight<3>(i);
         const F2 v = h[slot<3>(i)] * F2(iw);
-        Codec<S>::st(dst + (i * PS + cellA), v.v.x);
-        Codec<S>::st(dst + (i * PS + cellB), v.v.y);
+        Codec<S>::st(dst + (i * PS + dA), v.v.x);
+        Codec<S>::st(dst + (i * PS + dB), v.v.y);
     });
 }
 
@@ -108,7 +140,49 @@ void launch_pair(const void* src, void* dst, const void* Ff, const Params& p, cu
     const int half = p.nx / 2;
     const dim3 b = cell_block(half);
     const dim3 g((half + b.x - 1) / b.x, (p.ny + b.y - 1) / b.y, p.nz);
-    k_step_pair<S, FT><<<g, b, 0, st>>>((const S*)src, (S*)dst, (const float*)Ff, typed<float>(p));
+    k_step_pair<S, FT><<<g, b, 0, st>>>((const S*)src, (S*)dst, (const float*)Ff, typed<float>(p), Ring{});
+}
+
+// Two steps per pass (temporal blocking through the L2 cache). Steps t -> t+1 -> t+2 from the
+// full buffer A into the full buffer C; the intermediate state t+1 only ever exists in the
+// plane ring (see Ring), z-planes in groups of P:
+//   for each group [z0, z1):  ring planes z0 .. z1-1 of t+1 from A (reads A planes z0-1 .. z1),
+//                             then C planes z0-1 .. z1-2 of t+2 from the ring (reads ring planes
+//                             z0-2 .. z1-1, the last P+2 written; group 0 starts at plane 1);
+//   at the end:               C planes nz-1 and 0, whose pulls wrap around to ring planes 0, 1
+//                             (kept in the first two slots) and nz-2, nz-1.
+// Every cell is updated by the same kernel code as in single steps, so the result is bitwise
+// the same as two single steps. The ring needs at least P + 2 slots; the recently written ring
+// planes are read back while they are still in L2, so each cell's state crosses HBM once per
+// two steps (read in A, written in C).
+template <class S, class FT>
+int launch_pair_two_steps(const void* A, void* C, void* ring, int P, int slots, const void* Ff, const Params& p,
+                          cudaStream_t st) {
+    const int half = p.nx / 2;
+    const dim3 b = cell_block(half);
+    const PR<float> q = typed<float>(p);
+    const unsigned nxy = (unsigned)p.nx * p.ny;
+    Ring rg{(unsigned)(2 + slots) * nxy, nxy, slots, 0};
+    auto grid = [&](int planes) { return dim3((half + b.x - 1) / b.x, (p.ny + b.y - 1) / b.y, planes); };
+    int launches = 0;
+    for (int z0 = 0; z0 < p.nz; z0 += P) {
+        const int z1 = z0 + P < p.nz ? z0 + P : p.nz;
+        rg.z0 = z0;
+        k_step_pair<S, FT, false, true><<<grid(z1 - z0), b, 0, st>>>((const S*)A, (S*)ring, (const float*)Ff, q, rg);
+        const int c0 = z0 == 0 ? 1 : z0 - 1, c1 = z1 - 2;
+        launches += 1;
+        if (c1 >= c0) {
+            rg.z0 = c0;
+            k_step_pair<S, FT, true, false><<<grid(c1 - c0 + 1), b, 0, st>>>((const S*)ring, (S*)C, (const float*)Ff, q, rg);
+            launches += 1;
+        }
+    }
+    for (int z : {p.nz - 1, 0}) {
+        rg.z0 = z;
+        k_step_pair<S, FT, true, false><<<grid(1), b, 0, st>>>((const S*)ring, (S*)C, (const float*)Ff, q, rg);
+        launches += 1;
+    }
+    return launches;
 }
 
 // every feature combination the dispatcher in cm_kernels.cuh can pass (the general forms never

@@ -455,7 +455,10 @@ def test_pair_and_direct_kernels_agree(cm, storage):
     (dict(nx=128), "pair"), (dict(nx=128, storage="bf16"), "pair"), (dict(nx=96), "direct"),
     (dict(nx=128, storage="f64"), "direct"), (dict(nx=128, attractor="factorized"), "direct"),
     (dict(nx=128, bc=("bounceback", "periodic", "periodic")), "direct"), (dict(nx=128, kernel="direct"), "direct"),
-    (dict(nx=128, kernel="tma"), "tma"), (dict(nx=64, bc=("periodic", "periodic", "halo")), "pair")])
+    (dict(nx=128, kernel="tma"), "tma"), (dict(nx=64, bc=("periodic", "periodic", "halo")), "pair"),
+    (dict(nx=64, nz=16), "pair"), (dict(nx=64, nz=16, kernel="pair_two_steps"), "pair_two_steps"),
+    (dict(nx=64, nz=16, storage="bf16"), "pair"),
+    (dict(nx=64, nz=16, kernel="pair"), "pair"), (dict(nx=64, nz=16, bc=("periodic", "periodic", "halo")), "pair")])
 def test_automatic_kernel_choice(cm, kw, expect):
     args = dict(lattice="D3Q27", ny=4, nz=4, storage="f32")
     args.update(kw)
@@ -531,3 +534,60 @@ def test_graph_replayed_steps_equal_single_steps(cm, kernel):
     assert a.launch_count - la == b.launch_count - lb == 13
     a.close()
     b.close()
+
+
+TWO_STEP_CASES = {
+    "periodic_field_ragged_groups": dict(shape=(20, 6, 64), flow="tgv", kw=dict(tau=0.6, omega_bulk=1.0)),
+    "unforced_minimum_depth": dict(shape=(16, 5, 128), flow="tgv_unforced", kw=dict(tau=0.53)),
+    "walls_y_z_les_lid": dict(shape=(19, 9, 64), flow="channel",
+                              kw=dict(tau=0.52, smagorinsky_cs=0.15, van_driest=(26.0, 8.0),
+                                      bc=("periodic", "bounceback", "bounceback"),
+                                      wall_velocity=[[[0, 0, 0], [0, 0, 0]], [[0.02, 0, 0.01], [-0.03, 0.0, 0.0]],
+                                                     [[0.01, 0, 0], [0, 0.02, 0]]])),
+}
+
+
+@pytest.mark.parametrize("steps", [2, 7, 12])
+@pytest.mark.parametrize("name", list(TWO_STEP_CASES))
+def test_two_steps_per_pass_equal_single_steps_bitwise(cm, name, steps):
+    """The plane-ring schedule runs the same kernel code on every cell: bitwise equal states."""
+    case = dict(TWO_STEP_CASES[name], lattice="D3Q27")
+    rho, u, F = _inputs(case)
+    a, _ = _pair(cm, "D3Q27", case["shape"], "f32", rho, u, F, kernel="pair_two_steps", **case["kw"])
+    b, _ = _pair(cm, "D3Q27", case["shape"], "f32", rho, u, F, kernel="pair", **case["kw"])
+    assert a.step_kernel == "pair_two_steps" and b.step_kernel == "pair"
+    a.step(steps)
+    for _ in range(steps):
+        b.step(1)
+    assert torch.equal(a.get_state(), b.get_state())
+    # and again after a force change (the captured passes are dropped)
+    a.set_force((1e-5, -2e-5, 0.0))
+    b.set_force((1e-5, -2e-5, 0.0))
+    a.step(4)
+    b.step(4)
+    assert torch.equal(a.get_state(), b.get_state())
+    a.close()
+    b.close()
+
+
+def test_two_steps_per_pass_against_the_oracle(cm):
+    case = dict(TWO_STEP_CASES["walls_y_z_les_lid"], lattice="D3Q27")
+    rho, u, F = _inputs(case)
+    s, o = _pair(cm, "D3Q27", case["shape"], "f32", rho, u, F, kernel="pair_two_steps", **case["kw"])
+    assert s.step_kernel == "pair_two_steps"
+    s.step(20)
+    o.step(20)
+    _, ug = s.moments()
+    _, uo = o.moments()
+    assert H.rel_l2(ug, uo) < 1e-5
+    s.close()
+
+
+@pytest.mark.parametrize("kw", [dict(nz=15), dict(storage="bf16"), dict(nx=96), dict(bc=("periodic", "periodic", "halo")),
+                                dict(attractor="factorized")])
+def test_two_steps_requested_on_ineligible_config_is_rejected(cm, kw):
+    args = dict(lattice="D3Q27", nx=64, ny=4, nz=16, storage="f32", kernel="pair_two_steps")
+    args.update(kw)
+    with pytest.raises(cm.CmlbmError) as e:
+        cm.Solver(**args)
+    assert e.value.code == cm.ERR_UNSUPPORTED
