@@ -38,6 +38,7 @@ FALLBACK_HBM = 6800.0
 # bulk-viscosity rate of the trace of the second-order moments: free in the paper ("adjusted to
 # improve numerical stability"); at tau -> 1/2 a bulk rate equal to the shear rate is unstable
 OMEGA_BULK = 1.0
+HIT_TAU = 0.5005       # base relaxation time of the forced isotropic turbulence LES
 
 
 def parse():
@@ -46,12 +47,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=256, help="edge of the Taylor-Green box")
+    ap.add_argument("--n", type=int, default=256, help="edge of the cubic box")
     ap.add_argument("--no-forms", action="store_true", help="skip the secondary forms")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--form-steps", type=int, default=40)
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"],
-                    help="population storage of the timed Taylor-Green step (f32 is the headline)")
+                    help="population storage of the timed step (f32 is the headline)")
+    ap.add_argument("--flow", default="tgv", choices=["tgv", "hit"],
+                    help="timed workload: the Taylor-Green vortex (headline) or the forced isotropic "
+                         "turbulence LES (force field, Cs = 0.1) on the same n^3 box")
     ap.add_argument("--kernel", default="auto", choices=["auto", "direct", "pair", "pair_two_steps", "tma"],
                     help="step kernel: the library's choice (auto), one cell per thread (direct), two cells "
                          "per thread in packed FP32 (pair), or rows staged by TMA (tma)")
@@ -219,15 +223,23 @@ def time_steps(solver, steps, warmup, dist, stream):
 # ------------------------------------------------------------------------------------------
 # forms
 # ------------------------------------------------------------------------------------------
-def run_tgv(cm, n, storage, steps, warmup, dist, clocks=None, kernel="auto"):
+def run_tgv(cm, n, storage, steps, warmup, dist, clocks=None, kernel="auto", flow="tgv"):
     from paper_1202_6074_gb300 import workloads as W
 
     stream = torch.cuda.current_stream()
-    s = cm.Solver(lattice="D3Q27", nx=n, ny=n, nz=n, storage=storage, tau=tgv_tau(n), omega_bulk=OMEGA_BULK,
-                  kernel=kernel)
-    rho, u = W.taylor_green(n, n, n, u0=0.05, xp=torch, device="cuda")
-    s.init(rho, u)
-    del rho, u
+    if flow == "hit":
+        s = cm.Solver(lattice="D3Q27", nx=n, ny=n, nz=n, storage=storage, tau=HIT_TAU, smagorinsky_cs=0.1,
+                      omega_bulk=OMEGA_BULK, kernel=kernel)
+        F = W.hit_forcing(n, n, n, seed=1, xp=torch, device="cuda")
+        s.set_force((0, 0, 0), F)
+        del F
+        s.init()
+    else:
+        s = cm.Solver(lattice="D3Q27", nx=n, ny=n, nz=n, storage=storage, tau=tgv_tau(n), omega_bulk=OMEGA_BULK,
+                      kernel=kernel)
+        rho, u = W.taylor_green(n, n, n, u0=0.05, xp=torch, device="cuda")
+        s.init(rho, u)
+        del rho, u
     if clocks:
         clocks.start()
     ms, launches = time_steps(s, steps, warmup, dist, stream)
@@ -311,7 +323,7 @@ def run_slabs(cm, n, k, steps):
 def run_hit_les(cm, n, storage, steps, warmup, dist):
     from paper_1202_6074_gb300 import workloads as W
 
-    s = cm.Solver(lattice="D3Q27", nx=n, ny=n, nz=n, storage=storage, tau=0.5005, smagorinsky_cs=0.1,
+    s = cm.Solver(lattice="D3Q27", nx=n, ny=n, nz=n, storage=storage, tau=HIT_TAU, smagorinsky_cs=0.1,
                   omega_bulk=OMEGA_BULK)
     F = W.hit_forcing(n, n, n, seed=1, xp=torch, device="cuda")
     s.set_force((0, 0, 0), F)
@@ -342,7 +354,7 @@ def run_channel(cm, storage, steps, warmup, dist, nx=1024, ny=256, nz=256):
     return ms, launches
 
 
-def e2e(cm, n, storage, steps, kernel="auto", repeats=3):
+def e2e(cm, n, storage, steps, kernel="auto", repeats=5):
     """Whole job through the C ABI with host buffers: upload (rho, u) from pinned memory, init,
     `steps` steps, download (rho, u) and the FP64 reductions; wall clock around all of it. The
     job is repeated `repeats` times (a new handle each time) and the median run is reported: the
@@ -384,8 +396,7 @@ def e2e(cm, n, storage, steps, kernel="auto", repeats=3):
             "runs_MLUPS": [r[0] for r in runs]}
 
 
-def cpu_baseline(n=40, steps=4):
-    """The FP64 oracle on a bounded sample of the workload: a Taylor-Green box of n^3."""
+def _oracle_mlups(n, steps):
     from oracle.solver import OracleSim
     from oracle.collision import Params
     from paper_1202_6074_gb300 import workloads as W
@@ -396,20 +407,41 @@ def cpu_baseline(n=40, steps=4):
     t0 = time.perf_counter()
     o.step(steps)
     t1 = time.perf_counter()
-    return {"value": n ** 3 * steps / (t1 - t0) / 1e6, "unit": "MLUPS", "cores": torch.get_num_threads(),
-            "kind": "oracle", "sample": f"D3Q27 FP64 Taylor-Green {n}^3 x {steps} steps (same flow, smaller box)",
-            "seconds": t1 - t0}
+    return n ** 3 * steps / (t1 - t0) / 1e6, t1 - t0
+
+
+def cpu_baseline(n=64, steps=50, n1=40, steps1=4):
+    """The FP64 oracle on a bounded sample of the workload (a Taylor-Green box of n^3, about 10 s
+    on 16 host cores), plus a smaller sample on one core."""
+    import platform
+
+    v, sec = _oracle_mlups(n, steps)
+    threads = torch.get_num_threads()
+    torch.set_num_threads(1)
+    try:
+        v1, sec1 = _oracle_mlups(n1, steps1)
+    finally:
+        torch.set_num_threads(threads)
+    return {"value": v, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+            "sample": f"D3Q27 FP64 Taylor-Green {n}^3 x {steps} steps (same flow, smaller box)", "seconds": sec,
+            "host": {"machine": platform.machine(), "cpus": os.cpu_count(), "affinity": len(os.sched_getaffinity(0))},
+            "one_core": {"value": v1, "sample": f"{n1}^3 x {steps1} steps", "seconds": sec1}}
 
 
 # ------------------------------------------------------------------------------------------
 # arms
 # ------------------------------------------------------------------------------------------
-def workload_config(n, st, world):
+def workload_config(n, st, world, flow="tgv"):
     """The benchmark's workload description (shared by both arms)."""
     N = n ** 3
     half = BYTES_PER_CELL[("D3Q27", st)] / 2 * N
-    return {"workload": f"D3Q27 CM-LBM {st.upper()} decaying Taylor-Green vortex {n}^3 periodic, u0=0.05, "
-                        f"Re=1600, no LES (tau={tgv_tau(n):.6f}, bulk rate {OMEGA_BULK})",
+    if flow == "hit":
+        name = (f"D3Q27 CM-LBM {st.upper()} forced isotropic turbulence {n}^3 periodic, shells |k| <= 2 "
+                f"(seed 1), Smagorinsky Cs=0.1 (tau0={HIT_TAU}, bulk rate {OMEGA_BULK})")
+    else:
+        name = (f"D3Q27 CM-LBM {st.upper()} decaying Taylor-Green vortex {n}^3 periodic, u0=0.05, "
+                f"Re=1600, no LES (tau={tgv_tau(n):.6f}, bulk rate {OMEGA_BULK})")
+    return {"workload": name,
             "cells": N, "l2": "state 2 x %.2f GB %s 129 MB L2, no flush" % (half / 1e9, ">>" if half > 129e6 else "vs"),
             "parallelism": "replicas" if world > 1 else "single GPU"}
 
@@ -458,32 +490,35 @@ def our_arm(args, dist):
     pk, pk_kind = peaks()
     clocks = Clocks(dist.local)
     st = args.storage
-    ms, launches, ck, red, kname = run_tgv(cm, n, st, args.steps, args.warmup, dist, clocks, kernel=args.kernel)
+    hit = args.flow == "hit"
+    ms, launches, ck, red, kname = run_tgv(cm, n, st, args.steps, args.warmup, dist, clocks, kernel=args.kernel,
+                                           flow=args.flow)
     ms = dist.max(ms)
     per_launch_s = ms / 1e3 / args.steps
     value = dist.world * N * args.steps / (ms / 1e3) / 1e6
-    bpc = BYTES_PER_CELL[("D3Q27", st)]
+    bpc = BYTES_PER_CELL[("D3Q27", st)] + (12 if hit else 0)      # + the FP32 force field
     achieved = bpc * N / per_launch_s / 1e9
-    traffic_pc = measured_traffic(f"k_step_d3q27_{st}_periodic_{kname}")
+    traffic_pc = None if hit else measured_traffic(f"k_step_d3q27_{st}_periodic_{kname}")
     line = {
         "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": dist.world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": st, "data": "synthetic",
-        "config": workload_config(n, st, dist.world),
+        "config": workload_config(n, st, dist.world, args.flow),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"], "peak_kind": pk_kind,
                      "traffic": None if traffic_pc is None else traffic_pc * N,
                      "algorithmic_bytes_per_cell": bpc,
                      "kernel": {"tma": "k_step_tma", "pair": "k_step_pair", "direct": "k_step",
                                 "pair_two_steps": "k_step_pair (two steps per pass)"}[kname]
-                               + f"<D3Q27,{st},periodic>"},
+                               + f"<D3Q27,{st},periodic{',LES,force field' if hit else ''}>"},
         "clocks": ck,
         "gpu_launches": int(launches),
         "diagnostics": {"mass": red[0], "kinetic_energy": red[4]},
     }
     if dist.rank == 0:
         torch.cuda.empty_cache()
-        line["e2e"] = e2e(cm, n, st, E2E_STEPS, kernel=args.kernel)
+        # the end-to-end job is the Taylor-Green one (host fields rho, u in, rho, u out)
+        line["e2e"] = None if hit else e2e(cm, n, st, E2E_STEPS, kernel=args.kernel)
         forms = {}
         if not args.no_forms:
             fs = args.form_steps

@@ -216,6 +216,19 @@ __device__ __forceinline__ unsigned short ld_stream(const unsigned short* p) {
     return v;
 }
 
+__device__ __forceinline__ unsigned ld_stream(const unsigned* p) {
+    unsigned v;
+    asm("ld.global.nc.L2::256B.b32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float2 ld_stream(const float2* p) {
+    float2 v;
+    asm("ld.global.nc.L2::256B.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
+}
+
+// ld / st: one entry; ld2 / st2 (FP32 and 16-bit storage): the entries p[0], p[1] of two
+// adjacent cells in one access (p must be aligned to two entries), rounded as ld / st round
 template <class S> struct Codec;
 template <> struct Codec<double> {
     using R = double;
@@ -228,6 +241,8 @@ template <> struct Codec<float> {
     static __device__ __forceinline__ R ld(const float* p) { return ld_stream(p); }
     static __device__ __forceinline__ R ld_shared(const float* p) { return *p; }
     static __device__ __forceinline__ void st(float* p, R v) { *p = v; }
+    static __device__ __forceinline__ float2 ld2(const float* p) { return ld_stream(reinterpret_cast<const float2*>(p)); }
+    static __device__ __forceinline__ void st2(float* p, float a, float b) { *reinterpret_cast<float2*>(p) = make_float2(a, b); }
 };
 template <> struct Codec<__nv_bfloat16> {
     using R = float;
@@ -238,6 +253,13 @@ template <> struct Codec<__nv_bfloat16> {
         return __bfloat162float(__ushort_as_bfloat16(*reinterpret_cast<const unsigned short*>(p)));
     }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, R v) { *p = __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ float2 ld2(const __nv_bfloat16* p) {
+        const unsigned v = ld_stream(reinterpret_cast<const unsigned*>(p));   // BF16 = top half of an FP32
+        return make_float2(__uint_as_float(v << 16), __uint_as_float(v & 0xffff0000u));
+    }
+    static __device__ __forceinline__ void st2(__nv_bfloat16* p, float a, float b) {
+        *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
+    }
 };
 template <> struct Codec<__half> {
     using R = float;
@@ -248,6 +270,13 @@ template <> struct Codec<__half> {
         return __half2float(__ushort_as_half(*reinterpret_cast<const unsigned short*>(p)));
     }
     static __device__ __forceinline__ void st(__half* p, R v) { *p = __float2half_rn(v); }
+    static __device__ __forceinline__ float2 ld2(const __half* p) {
+        const unsigned v = ld_stream(reinterpret_cast<const unsigned*>(p));
+        return __half22float2(*reinterpret_cast<const __half2*>(&v));
+    }
+    static __device__ __forceinline__ void st2(__half* p, float a, float b) {
+        *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b);
+    }
 };
 
 // ------------------------------------------------------------------------------------------

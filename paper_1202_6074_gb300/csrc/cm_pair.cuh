@@ -5,12 +5,29 @@
 
 namespace cm {
 
-// Cells (x, y, z) and (x + nx/2, y, z) are updated together with the packed FP32 instructions
-// (R = F2). They share y and z, hence the y/z wall flags, the row offsets, and the van Driest
-// constant; x must be periodic. Each lane is rounded as the scalar FP32 arithmetic rounds it.
+// Two cells of a row, (x, y, z) and (x + nx/2, y, z) or the adjacent (x0, y, z) and
+// (x0 + 1, y, z), are updated together with the packed FP32 instructions (R = F2). They share y
+// and z, hence the y/z wall flags, the row offsets, and the van Driest constant; x must be
+// periodic. Each lane is rounded as the scalar FP32 arithmetic rounds it.
 #ifndef CM_PAIR_MIN_BLOCKS
 #define CM_PAIR_MIN_BLOCKS 4
 #endif
+// Resident blocks per SM the register budget is sized for: 4 (at most 128 registers) in
+// general; 5 (at most 102) for the unforced SIMPLE collision with 16-bit storage, which fits
+// without spills and, bound by instruction latency rather than by HBM, gains from the fifth
+// block (about 2 % on the Taylor-Green step; the forced forms spill at 5 and lose 5-15 %).
+template <class S, class FT>
+constexpr int pair_min_blocks() {
+    return (FT::SIMPLE && sizeof(S) == 2) ? CM_PAIR_MIN_BLOCKS + 1 : CM_PAIR_MIN_BLOCKS;
+}
+
+// Which two cells share a thread: (x, x + nx/2) or the adjacent (x0, x0 + 1), x0 even.
+// Adjacent cells read their e_x = 0 populations and write all their populations as one access
+// of two entries (e_x = +-1 populations stay two single-entry reads), which removes a third of
+// the memory instructions and half of the address arithmetic. Measured on the 256^3 steps:
+// +12 % (Taylor-Green) and +14 % (forced LES) at 16-bit storage, +3 % for the forced FP32 LES,
+// but -1 % for the unforced FP32 step, which stays on (x, x + nx/2).
+template <class S, class FT> constexpr bool pair_adjacent() { return sizeof(S) == 2 || !FT::SIMPLE; }
 
 // Plane ring of the two-steps-per-pass schedule (launch_pair_two_steps): the intermediate state
 // t+1 lives in a small buffer of z-planes instead of a full state buffer. Plane z sits in slot
@@ -90,13 +107,80 @@ __device__ __forceinline__ void gather_pair(const S* __restrict__ src, int x, in
             const float add = 6.f * eu * (cnt == 2 ? 0.5f : 1.f);
             h[slot<3>(i)] = F2(da + add, db + add) * F2(w);
         } else {
-            h[slot<3>(i)] = F2(Codec<S>::ld(src + (base + (unsigned)xa[a])), Codec<S>::ld(src + (base + (unsigned)xb[a]))) * F2(w);
+            if constexpr (sizeof(S) == 2)   // 64-bit row pointers (measured faster at 16-bit storage)
+                h[slot<3>(i)] = F2(Codec<S>::ld(src + xa[a] + base), Codec<S>::ld(src + xb[a] + base)) * F2(w);
+            else
+                h[slot<3>(i)] = F2(Codec<S>::ld(src + (base + (unsigned)xa[a])), Codec<S>::ld(src + (base + (unsigned)xb[a]))) * F2(w);
         }
     });
 }
 
-template <class S, class FT, bool RS = false, bool RD = false>
-__global__ void __launch_bounds__(kBlock, CM_PAIR_MIN_BLOCKS) k_step_pair(const S* __restrict__ src, S* __restrict__ dst,
+// The pull of the adjacent cells (x0, y, z) and (x0 + 1, y, z), x0 even, from a full state
+// buffer. Slot k <-> e_x = k - 1 reads columns x - e_x: c0[k] for the first cell, c1[k] for the
+// second; the e_x = 0 pair (x0, x0 + 1) is one aligned two-entry read (direction-plane
+// strides, row offsets and x0 are even).
+template <class S, bool WALLS>
+__device__ __forceinline__ void gather_adj(const S* __restrict__ src, int x0, int y, int z, const PR<float>& p,
+                                           F2 (&h)[27]) {
+    const unsigned PS = p.S;
+    const int c0[3] = {x0 + 1, x0, x0 == 0 ? p.nx - 1 : x0 - 1};
+    const int c1[3] = {x0 + 2 == p.nx ? 0 : x0 + 2, x0 + 1, x0};
+    int ys[3], zs[3];
+    bool yo[3] = {false, false, false}, zo[3] = {false, false, false};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        int sy = y + 1 - k, sz = z + 1 - k;
+        if (sy < 0 || sy >= p.ny) {
+            if (!WALLS || p.bc[1] != 1) sy += (sy < 0) ? p.ny : -p.ny;
+            else { yo[k] = true; sy = y; }
+        }
+        if (sz < 0 || sz >= p.nz) {
+            if (!WALLS || p.bc[2] != 1) sz += (sz < 0) ? p.wz : -p.wz;
+            else { zo[k] = true; sz = z; }
+        }
+        ys[k] = sy;
+        zs[k] = sz;
+    }
+    unsigned row[3][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) row[c][b] = (unsigned)((zs[c] * p.ny + ys[b]) * p.nx);
+    const unsigned own = (unsigned)((z * p.ny + y) * p.nx + x0);
+    sfor<27>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int a = Lat<3>::ex(i) + 1, b = Lat<3>::ey(i) + 1, c = Lat<3>::ez(i) + 1;
+        constexpr float w = (float)weight<3>(i);
+        const unsigned base = i * PS + row[c][b];
+        if constexpr (WALLS) {
+            const bool by = yo[b], bz = zo[c];
+            const bool bounced = by || bz;
+            const unsigned back = Lat<3>::opp(i) * PS + own;     // the cells' own reflected entries
+            float2 d;
+            if constexpr (a == 1) {
+                d = Codec<S>::ld2(src + (bounced ? back : base + (unsigned)x0));
+            } else {
+                d.x = Codec<S>::ld(src + (bounced ? back : base + (unsigned)c0[a]));
+                d.y = Codec<S>::ld(src + (bounced ? back + 1u : base + (unsigned)c1[a]));
+            }
+            constexpr int sy = (b == 2) ? 0 : 1, sz = (c == 2) ? 0 : 1;
+            float eu = 0.f;
+            if constexpr (b != 1) eu += by ? (float(Lat<3>::ex(i)) * p.uw[1][sy][0] + float(Lat<3>::ey(i)) * p.uw[1][sy][1] + float(Lat<3>::ez(i)) * p.uw[1][sy][2]) : 0.f;
+            if constexpr (c != 1) eu += bz ? (float(Lat<3>::ex(i)) * p.uw[2][sz][0] + float(Lat<3>::ey(i)) * p.uw[2][sz][1] + float(Lat<3>::ez(i)) * p.uw[2][sz][2]) : 0.f;
+            const int cnt = (int)by + (int)bz;
+            const float add = 6.f * eu * (cnt == 2 ? 0.5f : 1.f);
+            h[slot<3>(i)] = F2(d.x + add, d.y + add) * F2(w);
+        } else if constexpr (a == 1) {
+            const float2 d = Codec<S>::ld2(src + x0 + base);
+            h[slot<3>(i)] = F2(d.x, d.y) * F2(w);
+        } else {
+            h[slot<3>(i)] = F2(Codec<S>::ld(src + c0[a] + base), Codec<S>::ld(src + c1[a] + base)) * F2(w);
+        }
+    });
+}
+
+template <class S, class FT, bool RS = false, bool RD = false, bool ADJ = false>
+__global__ void __launch_bounds__(kBlock, pair_min_blocks<S, FT>()) k_step_pair(const S* __restrict__ src, S* __restrict__ dst,
                                                                           const float* __restrict__ Ff, PR<float> p,
                                                                           Ring ring) {
     const int half = p.nx >> 1;
@@ -104,12 +188,22 @@ __global__ void __launch_bounds__(kBlock, CM_PAIR_MIN_BLOCKS) k_step_pair(const 
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = (RS || RD) ? (int)blockIdx.z + ring.z0 : (int)blockIdx.z;
     if (x >= half || y >= p.ny) return;
+    static_assert(!ADJ || (!RS && !RD), "adjacent cells only between full state buffers");
     // global cells (force field) and the destination cells
-    const unsigned cellA = (unsigned)((z * p.ny + y) * p.nx + x), cellB = cellA + (unsigned)half;
+    const int xa = ADJ ? 2 * x : x;
+    const unsigned cellA = (unsigned)((z * p.ny + y) * p.nx + xa), cellB = cellA + (ADJ ? 1u : (unsigned)half);
     const unsigned dA = RD ? ring.plane(z) + (unsigned)(y * p.nx + x) : cellA, dB = dA + (unsigned)half;
     const unsigned PS = RD ? ring.stride : p.S;
     F2 h[27];
-    if constexpr (FT::WALLS) {
+    if constexpr (ADJ) {
+        if constexpr (FT::WALLS) {
+            const bool near = (p.bc[1] == 1 && (y == 0 || y == p.ny - 1)) || (p.bc[2] == 1 && (z == 0 || z == p.nz - 1));
+            if (near) gather_adj<S, true>(src, xa, y, z, p, h);
+            else gather_adj<S, false>(src, xa, y, z, p, h);
+        } else {
+            gather_adj<S, false>(src, xa, y, z, p, h);
+        }
+    } else if constexpr (FT::WALLS) {
         const bool near = (p.bc[1] == 1 && (y == 0 || y == p.ny - 1)) || (p.bc[2] == 1 && (z == 0 || z == p.nz - 1));
         if (near) gather_pair<S, true, RS>(src, x, y, z, p, h, ring);
         else gather_pair<S, false, RS>(src, x, y, z, p, h, ring);
@@ -119,8 +213,16 @@ __global__ void __launch_bounds__(kBlock, CM_PAIR_MIN_BLOCKS) k_step_pair(const 
     F2 F[3];
     if (FT::FIELD && p.has_field) {
         const unsigned N = p.N;
+        if constexpr (ADJ) {
 #pragma unroll
-        for (int d = 0; d < 3; ++d) F[d] = F2(__ldg(Ff + (d * N + cellA)), __ldg(Ff + (d * N + cellB)));
+            for (int d = 0; d < 3; ++d) {
+                const float2 f = __ldg(reinterpret_cast<const float2*>(Ff + (d * N + cellA)));
+                F[d] = F2(f.x, f.y);
+            }
+        } else {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) F[d] = F2(__ldg(Ff + (d * N + cellA)), __ldg(Ff + (d * N + cellB)));
+        }
     } else {
 #pragma unroll
         for (int d = 0; d < 3; ++d) F[d] = F2(p.F[d]);
@@ -130,8 +232,15 @@ __global__ void __launch_bounds__(kBlock, CM_PAIR_MIN_BLOCKS) k_step_pair(const 
         constexpr int i = decltype(I)::value;
         constexpr float iw = (float)inv_weight<3>(i);
         const F2 v = h[slot<3>(i)] * F2(iw);
-        Codec<S>::st(dst + (i * PS + dA), v.v.x);
-        Codec<S>::st(dst + (i * PS + dB), v.v.y);
+        if constexpr (ADJ) {
+            Codec<S>::st2(dst + dA + (size_t)PS * i, v.v.x, v.v.y);
+        } else if constexpr (sizeof(S) == 2) {
+            Codec<S>::st(dst + dA + (size_t)PS * i, v.v.x);
+            Codec<S>::st(dst + dB + (size_t)PS * i, v.v.y);
+        } else {
+            Codec<S>::st(dst + (i * PS + dA), v.v.x);
+            Codec<S>::st(dst + (i * PS + dB), v.v.y);
+        }
     });
 }
 
@@ -140,6 +249,16 @@ void launch_pair(const void* src, void* dst, const void* Ff, const Params& p, cu
     const int half = p.nx / 2;
     const dim3 b = cell_block(half);
     const dim3 g((half + b.x - 1) / b.x, (p.ny + b.y - 1) / b.y, p.nz);
+    // adjacent cells need both buffers aligned to two entries (buffers passed in by the caller
+    // may be offset); the force field is the library's own allocation
+    if constexpr (pair_adjacent<S, FT>()) {
+        const uintptr_t two = 2 * sizeof(S);
+        if ((uintptr_t)src % two == 0 && (uintptr_t)dst % two == 0) {
+            k_step_pair<S, FT, false, false, true><<<g, b, 0, st>>>((const S*)src, (S*)dst, (const float*)Ff,
+                                                                     typed<float>(p), Ring{});
+            return;
+        }
+    }
     k_step_pair<S, FT><<<g, b, 0, st>>>((const S*)src, (S*)dst, (const float*)Ff, typed<float>(p), Ring{});
 }
 

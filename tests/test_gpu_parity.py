@@ -423,6 +423,30 @@ def test_pair_kernel_one_step_elementwise(cm, name, storage):
     s.close()
 
 
+@pytest.mark.parametrize("storage", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("name", list(PAIR_CASES) + ["unforced_unit_rates_pair_walls_les"])
+def test_pair_kernel_cell_pairings_agree_bitwise(cm, name, storage):
+    """The two-cells-per-thread step pairs adjacent cells (x0, x0 + 1) when both state buffers
+    are aligned to two entries, and (x, x + nx/2) otherwise (buffers offset by one entry here).
+    Every cell goes through the same lane arithmetic either way: the bits must agree."""
+    case = PAIR_CASES.get(name) or CASES[name]
+    rho, u, F = _inputs(case)
+    s, _ = _pair(cm, case["lattice"], case["shape"], storage, rho, u, F, kernel="pair", **case["kw"])
+    s0 = s.get_state().reshape(-1)
+    n = s0.numel()
+    outs = []
+    for off in (0, 1):
+        a = torch.zeros(n + 1, dtype=s0.dtype, device="cuda")
+        b = torch.zeros_like(a)
+        src, dst = a[off:off + n], b[off:off + n]
+        src.copy_(s0)
+        s.step_buffers(src, dst)
+        outs.append(dst.clone())
+    torch.cuda.synchronize()
+    assert torch.equal(outs[0].view(torch.uint8), outs[1].view(torch.uint8))
+    s.close()
+
+
 @pytest.mark.parametrize("name", list(PAIR_CASES))
 def test_pair_kernel_fp32_trajectory(cm, name):
     case = PAIR_CASES[name]
