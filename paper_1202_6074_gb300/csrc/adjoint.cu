@@ -26,13 +26,18 @@ template <class R> __device__ __forceinline__ void fwd1_T(R& a, R& b, R& c, R u)
     b = m0 + e0 * m1 + e0 * e0 * m2;
     c = m0 + ep * m1 + ep * ep * m2;
 }
-// transpose of the 1D inverse transform (m0, m1, m2) -> (f-, f0, f+)
-template <class R> __device__ __forceinline__ void inv1_T(R& a, R& b, R& c, R u) {
+// transpose of the 1D inverse transform (m0, m1, m2) -> (f-, f0, f+), taken through its two
+// stages: the shift r1 = u m0 + m1, r2 = u^2 m0 + 2u m1 + m2 (raw moments), then
+// f-+ = (r2 -+ r1) / 2, f0 = m0 - r2. Transposed: r1bar = (fp - fm) / 2,
+// r2bar = (fm + fp) / 2 - f0, m0bar = f0 + u r1bar + u^2 r2bar, m1bar = r1bar + 2u r2bar,
+// m2bar = r2bar.
+template <class R> __device__ __forceinline__ void inv1_T(R& a, R& b, R& c, R u, R tu, R uu) {
     const R fm = a, f0 = b, fp = c;
-    const R uu = u * u;
-    a = R(0.5) * (uu - u) * fm + (R(1) - uu) * f0 + R(0.5) * (uu + u) * fp;
-    b = R(0.5) * (R(2) * u - R(1)) * fm - R(2) * u * f0 + R(0.5) * (R(2) * u + R(1)) * fp;
-    c = R(0.5) * fm - f0 + R(0.5) * fp;
+    const R r1 = R(0.5) * (fp - fm);
+    const R r2 = fma(R(0.5), fm + fp, -f0);
+    a = fma(u, r1, fma(uu, r2, f0));
+    b = fma(tu, r2, r1);
+    c = r2;
 }
 
 template <int D, class R> __device__ __forceinline__ void fwd_T(R (&m)[Lat<D>::Q], R ux, R uy, R uz) {
@@ -50,15 +55,16 @@ template <int D, class R> __device__ __forceinline__ void fwd_T(R (&m)[Lat<D>::Q
 }
 template <int D, class R> __device__ __forceinline__ void inv_T(R (&m)[Lat<D>::Q], R ux, R uy, R uz) {
     constexpr int NL = Lat<D>::Q / 3;
+    const R tx = ux + ux, ty = uy + uy, tz = uz + uz, qx = ux * ux, qy = uy * uy, qz = uz * uz;
 #pragma unroll
-    for (int l = 0; l < NL; ++l) inv1_T(m[3 * l], m[3 * l + 1], m[3 * l + 2], ux);
+    for (int l = 0; l < NL; ++l) inv1_T(m[3 * l], m[3 * l + 1], m[3 * l + 2], ux, tx, qx);
 #pragma unroll
     for (int c = 0; c < Lat<D>::NZ; ++c)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) inv1_T(m[9 * c + a], m[9 * c + 3 + a], m[9 * c + 6 + a], uy);
+        for (int a = 0; a < 3; ++a) inv1_T(m[9 * c + a], m[9 * c + 3 + a], m[9 * c + 6 + a], uy, ty, qy);
     if constexpr (D == 3) {
 #pragma unroll
-        for (int t = 0; t < 9; ++t) inv1_T(m[t], m[9 + t], m[18 + t], uz);
+        for (int t = 0; t < 9; ++t) inv1_T(m[t], m[9 + t], m[18 + t], uz, tz, qz);
     }
 }
 
@@ -66,17 +72,19 @@ template <int D, class R> __device__ __forceinline__ void inv_T(R (&m)[Lat<D>::Q
 template <int D, class R>
 __device__ __forceinline__ void shift_contract(const R (&bar)[Lat<D>::Q], const R (&val)[Lat<D>::Q], R out[3]) {
     constexpr int Q = Lat<D>::Q;
-    R sx = 0, sy = 0, sz = 0;
+    R s1[3] = {R(0), R(0), R(0)}, s2[3] = {R(0), R(0), R(0)};   // terms with exponent 1 / 2
 #pragma unroll
     for (int t = 0; t < Q; ++t) {
         const int a = ex_a(t), b = ex_b(t), c = ex_c(t);
-        if (a > 0) sx += R(a) * bar[t] * val[t > 0 ? t - 1 : 0];
-        if (b > 0) sy += R(b) * bar[t] * val[t > 2 ? t - 3 : 0];
-        if (c > 0) sz += R(c) * bar[t] * val[t > 8 ? t - 9 : 0];
+        if (a == 1) s1[0] = fma(bar[t], val[t > 0 ? t - 1 : 0], s1[0]);
+        if (a == 2) s2[0] = fma(bar[t], val[t > 0 ? t - 1 : 0], s2[0]);
+        if (b == 1) s1[1] = fma(bar[t], val[t > 2 ? t - 3 : 0], s1[1]);
+        if (b == 2) s2[1] = fma(bar[t], val[t > 2 ? t - 3 : 0], s2[1]);
+        if (c == 1) s1[2] = fma(bar[t], val[t > 8 ? t - 9 : 0], s1[2]);
+        if (c == 2) s2[2] = fma(bar[t], val[t > 8 ? t - 9 : 0], s2[2]);
     }
-    out[0] = sx;
-    out[1] = sy;
-    out[2] = sz;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) out[d] = fma(R(2), s2[d], s1[d]);
 }
 
 // Source index of direction i for the pull at (x, y, z): (direction, cell) of the element read.
@@ -135,8 +143,9 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_terminal(const S* __restrict
     for (int d = 0; d < D; ++d) dLdF[d * p.N + cell] += (double)(R(0.5) * mu[d] * irho);
 }
 
-// 5 resident blocks of 128 threads (at most 102 registers) with the L2 prefetch below measured
-// fastest at 128^3 and 256^3: 13.3 G cells/s against 9.5 without either (one block, 128 registers)
+// 5 resident blocks of 128 threads (at most 102 registers, a 64-byte spill) with the L2
+// prefetch below measured fastest at 128^3 and 256^3: 14.0 G cells/s at 256^3, against 13.4
+// with 4 blocks (no spill) and 9.5 with neither the prefetch nor the fifth block
 #ifndef CM_ADJ_MIN_BLOCKS
 #define CM_ADJ_MIN_BLOCKS 5
 #endif
@@ -156,13 +165,16 @@ __global__ void __launch_bounds__(kBlock, CM_ADJ_MIN_BLOCKS) k_adjoint_step(cons
     const int z = blockIdx.z;
     if (x >= p.nx || y >= p.ny) return;
     const unsigned cell = (unsigned)((z * p.ny + y) * p.nx + x);
+    const size_t NN = p.N;
+    const R* __restrict__ lam_c = lam_in + cell;      // lambda_{t+1} of this cell: lam_c[i N]
+    double* __restrict__ dF_c = dLdF + cell;
     if (CM_ADJ_PREFETCH) {
         // lambda_{t+1} and the dL/dF accumulator are needed only after the forward
         // recomputation: start bringing them into L2 now so that their loads do not stall
 #pragma unroll
-        for (int i = 0; i < Q; ++i) prefetch_l2(lam_in + ((unsigned)i * p.N + cell));
+        for (int i = 0; i < Q; ++i) prefetch_l2(lam_c + NN * i);
 #pragma unroll
-        for (int d = 0; d < D; ++d) prefetch_l2(dLdF + ((unsigned)d * p.N + cell));
+        for (int d = 0; d < D; ++d) prefetch_l2(dF_c + NN * d);
     }
 
     // ---- forward recomputation (plain central moments of fbar) ----
@@ -239,7 +251,7 @@ __global__ void __launch_bounds__(kBlock, CM_ADJ_MIN_BLOCKS) k_adjoint_step(cons
     // ---- reverse ----
     R L[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) L[slot<D>(i)] = __ldg(lam_in + (long long)i * p.N + cell);
+    for (int i = 0; i < Q; ++i) L[slot<D>(i)] = __ldg(lam_c + NN * i);
     inv_T<D, R>(L, u[0], u[1], u[2]);           // L = postbar
     R ub[3];
     shift_contract<D, R>(L, B, ub);              // inverse-transform u derivative
@@ -250,9 +262,16 @@ __global__ void __launch_bounds__(kBlock, CM_ADJ_MIN_BLOCKS) k_adjoint_step(cons
     Fb[1] += L[midx(0, 1, 0)];
     if constexpr (D == 3) Fb[2] += L[midx(0, 0, 1)];
 
-    // orders >= 3, decreasing; B is reused as kappabar accumulators
+    // orders >= 3, decreasing; B is reused as kappabar accumulators. The source term of moment t
+    // along axis d is alpha_d (F_d / rho) kappa_(t - e_d): its derivatives are gathered in
+    // G1 / G2 (terms with exponent 1 / 2) as sum kappa_(t - e_d) sbar_t, which give the F and rho
+    // adjoints once at the end: Fbar_d += G_d / rho, rhobar -= (F_d / rho) G_d / rho.
 #pragma unroll
     for (int t = 0; t < Q; ++t) B[t] = R(0);
+    R G1[3] = {R(0), R(0), R(0)}, G2[3] = {R(0), R(0), R(0)};
+    const R hw3 = fma(R(-0.5), w3, R(1)), hw4 = fma(R(-0.5), w4, R(1));
+    const R om3 = R(1) - w3, om4 = R(1) - w4;
+    const R aFr[2][3] = {{Fr[0], Fr[1], Fr[2]}, {Fr[0] + Fr[0], Fr[1] + Fr[1], Fr[2] + Fr[2]}};
     sfor<2 * D + 1>([&](auto NI) {
         constexpr int n = 2 * D - decltype(NI)::value;
         sfor<Q>([&](auto TI) {
@@ -260,18 +279,32 @@ __global__ void __launch_bounds__(kBlock, CM_ADJ_MIN_BLOCKS) k_adjoint_step(cons
             if constexpr (n >= 3 && ord(t) == n) {
                 constexpr int a = ex_a(t), b = ex_b(t), c = ex_c(t);
                 constexpr bool even = (a % 2 == 0) && (b % 2 == 0) && (c % 2 == 0);
-                constexpr R cM = even ? (R)third_pow((a == 2) + (b == 2) + (c == 2)) : R(0);
                 const R w = (n == 3) ? w3 : w4;
                 const R pb = L[t];
-                const R sb = (R(1) - R(0.5) * w) * pb + R(0.5) * B[t];
-                rb += w * cM * pb;
-                L[t] = (R(1) - w) * pb + B[t];       // kbarbar
-                if constexpr (a > 0) { const R kv = K[t - 1]; Fb[0] += R(a) * kv * irho * sb; rb -= R(a) * Fr[0] * irho * kv * sb; B[t - 1] += R(a) * Fr[0] * sb; }
-                if constexpr (b > 0) { const R kv = K[t - 3]; Fb[1] += R(b) * kv * irho * sb; rb -= R(b) * Fr[1] * irho * kv * sb; B[t - 3] += R(b) * Fr[1] * sb; }
-                if constexpr (c > 0) { const R kv = K[t - 9]; Fb[2] += R(c) * kv * irho * sb; rb -= R(c) * Fr[2] * irho * kv * sb; B[t - 9] += R(c) * Fr[2] * sb; }
+                const R sb = fma((n == 3) ? hw3 : hw4, pb, R(0.5) * B[t]);
+                if constexpr (even) {
+                    constexpr R cM = (R)third_pow((a == 2) + (b == 2) + (c == 2));
+                    rb = fma(w * cM, pb, rb);
+                }
+                L[t] = fma((n == 3) ? om3 : om4, pb, B[t]);       // kbarbar
+                if constexpr (a == 1) G1[0] = fma(K[t - 1], sb, G1[0]);
+                if constexpr (a == 2) G2[0] = fma(K[t - 1], sb, G2[0]);
+                if constexpr (a > 0) B[t - 1] = fma(aFr[a - 1][0], sb, B[t - 1]);
+                if constexpr (b == 1) G1[1] = fma(K[t - 3], sb, G1[1]);
+                if constexpr (b == 2) G2[1] = fma(K[t - 3], sb, G2[1]);
+                if constexpr (b > 0) B[t - 3] = fma(aFr[b - 1][1], sb, B[t - 3]);
+                if constexpr (c == 1) G1[2] = fma(K[t - 9], sb, G1[2]);
+                if constexpr (c == 2) G2[2] = fma(K[t - 9], sb, G2[2]);
+                if constexpr (c > 0) B[t - 9] = fma(aFr[c - 1][2], sb, B[t - 9]);
             }
         });
     });
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        const R G = fma(R(2), G2[d], G1[d]) * irho;
+        Fb[d] += G;
+        rb = fma(-Fr[d], G, rb);
+    }
     // order 2
     {
         const int dg[3] = {midx(2, 0, 0), midx(0, 2, 0), midx(0, 0, 2)};
@@ -305,10 +338,24 @@ __global__ void __launch_bounds__(kBlock, CM_ADJ_MIN_BLOCKS) k_adjoint_step(cons
 
     // u = (sum g e + F/2) / rho, rho = sum g
     const R ue = -(ub[0] * u[0] + ub[1] * u[1] + ub[2] * u[2]) * irho;
+    // L_t += rb + ue + (ub . e_t) / rho, built up axis by axis: X_k = c0 + (k - 1) cx,
+    // Y_kj = X_k + (j - 1) cy, then + (l - 1) cz
+    {
+        const R c0 = rb + ue, cx = ub[0] * irho, cy = ub[1] * irho, cz = ub[2] * irho;
+        const R X[3] = {c0 - cx, c0, c0 + cx};
+        R Y[9];
 #pragma unroll
-    for (int t = 0; t < Q; ++t) {
-        const R e0 = R(ex_a(t) - 1), e1 = R(ex_b(t) - 1), e2 = R(ex_c(t) - 1);
-        L[t] += rb + ue + irho * (ub[0] * e0 + ub[1] * e1 + (D == 3 ? ub[2] * e2 : R(0)));
+        for (int k = 0; k < 3; ++k) {
+            Y[3 + k] = X[k];
+            Y[k] = X[k] - cy;
+            Y[6 + k] = X[k] + cy;
+        }
+#pragma unroll
+        for (int t = 0; t < Q; ++t) {
+            const int l = t / 9;
+            const R add = (D == 2 || l == 1) ? Y[t % 9] : (l == 0) ? Y[t % 9] - cz : Y[t % 9] + cz;
+            L[t] += add;
+        }
     }
     Fb[0] += R(0.5) * irho * ub[0];
     Fb[1] += R(0.5) * irho * ub[1];
@@ -323,7 +370,7 @@ __global__ void __launch_bounds__(kBlock, CM_ADJ_MIN_BLOCKS) k_adjoint_step(cons
         lam_out[(unsigned)dir * p.N + sc] = L[slot<D>(i)];
     }
 #pragma unroll
-    for (int d = 0; d < D; ++d) dLdF[d * p.N + cell] += (double)Fb[d];
+    for (int d = 0; d < D; ++d) dF_c[NN * d] += (double)Fb[d];
 }
 
 }  // namespace
