@@ -223,7 +223,7 @@ def time_steps(solver, steps, warmup, dist, stream):
 # ------------------------------------------------------------------------------------------
 # forms
 # ------------------------------------------------------------------------------------------
-def run_tgv(cm, n, storage, steps, warmup, dist, clocks=None, kernel="auto", flow="tgv"):
+def run_tgv(cm, n, storage, steps, warmup, dist, clocks=None, kernel="auto", flow="tgv", **form):
     from paper_1202_6074_gb300 import workloads as W
 
     stream = torch.cuda.current_stream()
@@ -236,7 +236,7 @@ def run_tgv(cm, n, storage, steps, warmup, dist, clocks=None, kernel="auto", flo
         s.init()
     else:
         s = cm.Solver(lattice="D3Q27", nx=n, ny=n, nz=n, storage=storage, tau=tgv_tau(n), omega_bulk=OMEGA_BULK,
-                      kernel=kernel)
+                      kernel=kernel, **form)
         rho, u = W.taylor_green(n, n, n, u0=0.05, xp=torch, device="cuda")
         s.init(rho, u)
         del rho, u
@@ -527,6 +527,14 @@ def our_arm(args, dist):
                 sec = m / 1e3 / fs
                 forms[f"tgv{n}_{st}"] = {"MLUPS": N / sec / 1e6, "hbm_frac": BYTES_PER_CELL[("D3Q27", st)] * N / sec / 1e9
                                          / pk["hbm_gbs"], "steps": fs}
+            # the general collision forms (Secs. 12 and 13) on the same flow
+            for name, form in (("factorized", dict(attractor="factorized")),
+                               ("reduced", dict(reduced_compressibility=True, rho0=1.0))):
+                for st in ("f32", "bf16"):
+                    m, l, _, _, _ = run_tgv(cm, n, st, fs, 3, Dist0(), **form)
+                    sec = m / 1e3 / fs
+                    forms[f"tgv{n}_{name}_{st}"] = {"MLUPS": N / sec / 1e6, "hbm_frac": BYTES_PER_CELL[("D3Q27", st)] * N
+                                                    / sec / 1e9 / pk["hbm_gbs"], "steps": fs}
             nh = 512
             for st in ("f32", "bf16", "f16"):
                 try:

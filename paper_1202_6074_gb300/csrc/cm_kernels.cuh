@@ -202,7 +202,7 @@ inline bool has_walls(const Params& p) { return p.bc[0] == 1 || p.bc[1] == 1 || 
 template <int D, class S, class FT>
 void launch_step_ft(const void* src, void* dst, const void* Ff, const Params& p, cudaStream_t st) {
     using R = typename Codec<S>::R;
-    if constexpr (D == 3 && sizeof(R) == 4 && !FT::GEN) {
+    if constexpr (D == 3 && sizeof(R) == 4) {
         if (p.pair) {
             launch_pair<S, FT>(src, dst, Ff, p, st);
             return;

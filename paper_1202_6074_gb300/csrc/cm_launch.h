@@ -31,11 +31,10 @@ cudaError_t launch_adjoint_step(const void* state, const void* Ff, const Params&
 constexpr int kReduceMaxBlocks = 1216;
 
 // The two-cells-per-thread step (k_step_pair) covers D3Q27 with FP32 arithmetic, periodic x,
-// nx a multiple of 64 (each warp's 32 lanes read 32 consecutive cells of both halves of the
-// row) and the standard collision (the factorized / reduced forms would spill at its register
-// budget).
+// and nx a multiple of 64 (each warp's 32 lanes read 32 consecutive cells, or both halves of
+// the row), in every collision form.
 inline bool pair_eligible(const Params& p, int D, bool fp32_arith) {
-    return D == 3 && fp32_arith && p.bc[0] == 0 && p.nx % 64 == 0 && p.attractor == 0 && !p.reduced;
+    return D == 3 && fp32_arith && p.bc[0] == 0 && p.nx % 64 == 0;
 }
 
 // Two steps per pass for FP32 storage (launch_pair_two_steps, inst_pair_tb_f32.cu): planes in
@@ -43,7 +42,8 @@ inline bool pair_eligible(const Params& p, int D, bool fp32_arith) {
 constexpr int kTwoStepGroup = 8;
 constexpr int kTwoStepRing = kTwoStepGroup + 2;     // the planes a group's second step reads
 inline bool two_steps_eligible(const Params& p, int D, int storage_f32, bool slab) {
-    return storage_f32 && !slab && pair_eligible(p, D, true) && p.nz >= 2 * kTwoStepGroup;
+    return storage_f32 && !slab && pair_eligible(p, D, true) && p.nz >= 2 * kTwoStepGroup && p.attractor == 0 &&
+           !p.reduced;
 }
 // enqueue one pass (steps t -> t+2) from A into C; returns the number of kernel launches or -1
 int launch_two_steps_f32(const void* A, void* C, void* ring, const void* Ff, const Params& p, cudaStream_t st);

@@ -12,13 +12,19 @@ namespace cm {
 #ifndef CM_PAIR_MIN_BLOCKS
 #define CM_PAIR_MIN_BLOCKS 4
 #endif
-// Resident blocks per SM the register budget is sized for: 4 (at most 128 registers) in
-// general; 5 (at most 102) for the unforced SIMPLE collision with 16-bit storage, which fits
-// without spills and, bound by instruction latency rather than by HBM, gains from the fifth
-// block (about 2 % on the Taylor-Green step; the forced forms spill at 5 and lose 5-15 %).
+// Resident blocks per SM the register budget is sized for. The 16-bit steps are bound by
+// instruction latency rather than by HBM and gain from more resident warps where the registers
+// allow: 6 blocks (at most 80 registers, a 4-byte spill) for the unforced SIMPLE collision,
+// +2 %; 5 (at most 96, an 84-byte spill) for forced steps without a force field, +5 % on the
+// channel. A force field (the isotropic turbulence LES) loses 1 % at 5 blocks and stays at 4
+// (at most 128 registers), as do the general forms (they spill twice as much at 5) and all
+// FP32 steps (the forced FP32 LES loses 7 % at 5).
 template <class S, class FT>
 constexpr int pair_min_blocks() {
-    return (FT::SIMPLE && sizeof(S) == 2) ? CM_PAIR_MIN_BLOCKS + 1 : CM_PAIR_MIN_BLOCKS;
+    if constexpr (sizeof(S) == 2)
+        return FT::SIMPLE ? CM_PAIR_MIN_BLOCKS + 2
+                          : (!FT::FIELD && !FT::GEN ? CM_PAIR_MIN_BLOCKS + 1 : CM_PAIR_MIN_BLOCKS);
+    return CM_PAIR_MIN_BLOCKS;
 }
 
 // Which two cells share a thread: (x, x + nx/2) or the adjacent (x0, x0 + 1), x0 even.
@@ -304,8 +310,7 @@ int launch_pair_two_steps(const void* A, void* C, void* ring, int P, int slots, 
     return launches;
 }
 
-// every feature combination the dispatcher in cm_kernels.cuh can pass (the general forms never
-// take this kernel)
+// every feature combination the dispatcher in cm_kernels.cuh can pass
 #define CM_PAIR_INSTANTIATE(S)                                                                              \
     template void launch_pair<S, Feat<false, false, false, false>>(const void*, void*, const void*, const Params&, cudaStream_t); \
     template void launch_pair<S, Feat<false, false, true, false>>(const void*, void*, const void*, const Params&, cudaStream_t);  \
@@ -319,5 +324,17 @@ int launch_pair_two_steps(const void* A, void* C, void* ring, int P, int slots, 
     template void launch_pair<S, Feat<false, true, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);  \
     template void launch_pair<S, Feat<true, false, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);  \
     template void launch_pair<S, Feat<true, true, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);
+
+// the general forms (factorized attractor, reduced compressibility), in translation units of
+// their own so that the library builds in parallel
+#define CM_PAIR_INSTANTIATE_GEN(S)                                                                          \
+    template void launch_pair<S, Feat<false, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t); \
+    template void launch_pair<S, Feat<false, false, true, true>>(const void*, void*, const void*, const Params&, cudaStream_t);  \
+    template void launch_pair<S, Feat<false, true, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);  \
+    template void launch_pair<S, Feat<false, true, true, true>>(const void*, void*, const void*, const Params&, cudaStream_t);   \
+    template void launch_pair<S, Feat<true, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);  \
+    template void launch_pair<S, Feat<true, false, true, true>>(const void*, void*, const void*, const Params&, cudaStream_t);   \
+    template void launch_pair<S, Feat<true, true, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);   \
+    template void launch_pair<S, Feat<true, true, true, true>>(const void*, void*, const void*, const Params&, cudaStream_t);
 
 }  // namespace cm

@@ -1,0 +1,6 @@
+// Two-cells-per-thread step kernels of the general collision forms for __half storage (see cm_pair.cuh).
+#include "cm_pair.cuh"
+
+namespace cm {
+CM_PAIR_INSTANTIATE_GEN(__half)
+}  // namespace cm

@@ -393,6 +393,11 @@ def test_tma_requested_on_ineligible_config_is_rejected(cm):
 
 # D3Q27 cases the two-cells-per-thread kernel takes (periodic x, nx a multiple of 64)
 PAIR_CASES = {
+    "pair_factorized_field": dict(lattice="D3Q27", shape=(5, 6, 64), flow="tgv",
+                                  kw=dict(tau=0.58, omega_3=1.1, omega_4=1.3, attractor="factorized")),
+    "pair_reduced_walls_les": dict(lattice="D3Q27", shape=(5, 8, 128), flow="channel",
+                                   kw=dict(tau=0.6, reduced_compressibility=True, rho0=1.02, smagorinsky_cs=0.1,
+                                           bc=("periodic", "bounceback", "periodic"))),
     "pair_periodic_field": dict(lattice="D3Q27", shape=(5, 7, 128), flow="tgv", kw=dict(tau=0.6, omega_bulk=1.0)),
     "pair_walls_les_vd": dict(lattice="D3Q27", shape=(6, 9, 64), flow="channel",
                               kw=dict(tau=0.52, smagorinsky_cs=0.15, van_driest=(26.0, 8.0),
@@ -477,7 +482,8 @@ def test_pair_and_direct_kernels_agree(cm, storage):
 
 @pytest.mark.parametrize("kw,expect", [
     (dict(nx=128), "pair"), (dict(nx=128, storage="bf16"), "pair"), (dict(nx=96), "direct"),
-    (dict(nx=128, storage="f64"), "direct"), (dict(nx=128, attractor="factorized"), "direct"),
+    (dict(nx=128, storage="f64"), "direct"), (dict(nx=128, attractor="factorized"), "pair"),
+    (dict(nx=128, reduced_compressibility=True, storage="f16"), "pair"), (dict(nx=96, attractor="factorized"), "direct"),
     (dict(nx=128, bc=("bounceback", "periodic", "periodic")), "direct"), (dict(nx=128, kernel="direct"), "direct"),
     (dict(nx=128, kernel="tma"), "tma"), (dict(nx=64, bc=("periodic", "periodic", "halo")), "pair"),
     (dict(nx=64, nz=16), "pair"), (dict(nx=64, nz=16, kernel="pair_two_steps"), "pair_two_steps"),
@@ -492,7 +498,7 @@ def test_automatic_kernel_choice(cm, kw, expect):
 
 
 @pytest.mark.parametrize("kw", [dict(nx=96), dict(nx=128, bc=("bounceback", "periodic", "periodic")),
-                                dict(nx=128, attractor="factorized"), dict(nx=128, storage="f64"),
+                                dict(nx=96, attractor="factorized"), dict(nx=128, storage="f64"),
                                 dict(nx=128, lattice="D2Q9", nz=1)])
 def test_pair_requested_on_ineligible_config_is_rejected(cm, kw):
     args = dict(lattice="D3Q27", ny=4, nz=4, storage="f32", kernel="pair")
