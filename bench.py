@@ -39,6 +39,7 @@ FALLBACK_HBM = 6800.0
 # improve numerical stability"); at tau -> 1/2 a bulk rate equal to the shear rate is unstable
 OMEGA_BULK = 1.0
 HIT_TAU = 0.5005       # base relaxation time of the forced isotropic turbulence LES
+FILTERED_BYTES_PER_CELL = 136 + 36 + 40 + 228
 
 
 def parse():
@@ -294,7 +295,12 @@ def run_filtered(cm, n, steps):
     ms = _events_ms(lambda: s.step_filtered(steps, 0.1), stream)
     launches = s.launch_count - l0
     s.close()
-    return {"MLUPS": n ** 3 * steps / (ms / 1e3) / 1e6, "steps": steps, "launches_per_step": launches / steps}
+    mlups = n ** 3 * steps / (ms / 1e3) / 1e6
+    # bytes per cell of one filtered step: (rho, u) pass 108 + 12 read, 16 written; eddy stress
+    # 12 read, 24 written; closure force 24 + 4 read, 12 written; step 216 + 12
+    bpc = FILTERED_BYTES_PER_CELL
+    return {"MLUPS": mlups, "hbm_frac": bpc * mlups / 1e3 / peaks()[0]["hbm_gbs"], "bytes_per_cell": bpc,
+            "steps": steps, "launches_per_step": launches / steps}
 
 
 def run_slabs(cm, n, k, steps):
