@@ -166,7 +166,9 @@ CMLBM_API int cmlbm_set_force(cmlbm_t* h, const double uniform[3], const double*
 /* Initialise the state so that the next pull returns fbar = f^M(rho, u) - S/2 with the
  * current force, S evaluated at the Maxwellian moments (paper silent on initialisation;
  * the special case noted under Eq. exactidentitycomponents). rho [N] and u [3][N] are FP64
- * on `where`; rho NULL means 1, u NULL means 0. */
+ * on `where`; rho NULL means 1, u NULL means 0. With CMLBM_HOST, page-locked buffers that the
+ * CUDA runtime maps for the device (cudaHostAlloc, cudaMallocHost) are read in place by the
+ * init kernel; other host memory is staged through a device buffer. */
 CMLBM_API int cmlbm_init(cmlbm_t* h, const double* rho, const double* u, int where);
 
 /* Advance nsteps stream-and-collide steps (nsteps >= 0): the pull of Eq. cascadedstreaming1
@@ -183,7 +185,9 @@ CMLBM_API int cmlbm_step_buffers(cmlbm_t* h, const void* src, void* dst);
 
 /* Density [N] and velocity [3][N] (FP64) of the current pre-collision field (pull of the
  * stored state): Eqs. densitycalculation and velocitycalculation (reduced-compressibility
- * form: u = (sum fbar e + F/2) / rho0). Either pointer may be NULL. */
+ * form: u = (sum fbar e + F/2) / rho0). Either pointer may be NULL. With CMLBM_HOST,
+ * page-locked mapped buffers are written in place by the moments kernel (other host memory
+ * through a device staging buffer); the call returns when the values are in host memory. */
 CMLBM_API int cmlbm_moments(cmlbm_t* h, double* rho, double* u, int where);
 
 /* Same as cmlbm_moments for an arbitrary state buffer (device, handle layout). */

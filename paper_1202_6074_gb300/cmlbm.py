@@ -230,10 +230,19 @@ class Solver:
         self._check(self.lib.cmlbm_set_force(self.h, _as_vec3(uniform), _ptr(field), where))
 
     def init(self, rho=None, u=None):
-        host = isinstance(rho, np.ndarray) or isinstance(u, np.ndarray)
+        """Equilibrium initial state from FP64 fields: CUDA tensors, or host data (numpy arrays
+        or CPU tensors; page-locked CPU tensors are read in place by the init kernel)."""
+        def on_host(t):
+            return isinstance(t, np.ndarray) or (isinstance(t, torch.Tensor) and t.device.type == "cpu")
+        host = on_host(rho) or on_host(u)
         if host:
-            rho = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64)
-            u = None if u is None else np.ascontiguousarray(u, dtype=np.float64)
+            def prep(t):
+                if t is None:
+                    return None
+                if isinstance(t, torch.Tensor) and t.dtype == torch.float64 and t.is_contiguous():
+                    return t
+                return np.ascontiguousarray(t.numpy() if isinstance(t, torch.Tensor) else t, dtype=np.float64)
+            rho, u = prep(rho), prep(u)
         else:
             rho = None if rho is None else rho.to(self.device, torch.float64).contiguous()
             u = None if u is None else u.to(self.device, torch.float64).contiguous()
@@ -253,11 +262,16 @@ class Solver:
     def step_buffers(self, src, dst):
         self._check(self.lib.cmlbm_step_buffers(self.h, _ptr(src), _ptr(dst)))
 
-    def moments(self, state=None, host=False):
-        """(rho [nz,ny,nx], u [3,nz,ny,nx]) as float64; CUDA tensors, or numpy when host=True."""
+    def moments(self, state=None, host=False, out=None):
+        """(rho [nz,ny,nx], u [3,nz,ny,nx]) as float64; CUDA tensors, or host data when host=True
+        (new numpy arrays, or the caller's `out` = (rho, u) float64 host buffers; page-locked CPU
+        tensors are written in place by the moments kernel)."""
         if host:
-            rho = np.empty(self.shape)
-            u = np.empty((3,) + self.shape)
+            if out is None:
+                rho = np.empty(self.shape)
+                u = np.empty((3,) + self.shape)
+            else:
+                rho, u = out
             self._check(self.lib.cmlbm_moments(self.h, _ptr(rho), _ptr(u), HOST))
             return rho, u
         rho = torch.empty(self.shape, dtype=torch.float64, device=self.device)

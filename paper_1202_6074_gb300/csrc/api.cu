@@ -447,6 +447,20 @@ int cmlbm_set_force(cmlbm_t* h, const double uniform[3], const double* field, in
     return CMLBM_OK;
 }
 
+// The device address of page-locked host memory that the CUDA runtime maps into the device's
+// address space (cudaHostAlloc / cudaMallocHost, or cudaHostRegister with mapping): kernels read
+// and write it directly over the host link, with no staging copy. nullptr for any other pointer
+// (pageable memory goes through the device staging buffer and cudaMemcpyAsync).
+static void* mapped_host(const void* p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return (a.type == cudaMemoryTypeHost && a.devicePointer) ? a.devicePointer : nullptr;
+}
+
 int cmlbm_init(cmlbm_t* h, const double* rho, const double* u, int where) {
     if (!h) return CMLBM_ERR_INVALID;
     if (where != CMLBM_DEVICE && where != CMLBM_HOST) return fail(h, CMLBM_ERR_INVALID, "bad `where`");
@@ -462,7 +476,13 @@ int cmlbm_init(cmlbm_t* h, const double* rho, const double* u, int where) {
     };
     const double* drho = rho;
     const double* du = u;
-    if (where == CMLBM_HOST && (rho || u)) {
+    const double* mrho = (const double*)mapped_host(rho);
+    const double* mu = (const double*)mapped_host(u);
+    if (where == CMLBM_HOST && (!rho || mrho) && (!u || mu)) {
+        // page-locked fields: the init kernel reads them in place
+        drho = mrho;
+        du = mu;
+    } else if (where == CMLBM_HOST && (rho || u)) {
         int rc = ensure_stage(h);
         if (rc) return rc;
         if (rho) {
@@ -559,6 +579,16 @@ int cmlbm_moments(cmlbm_t* h, double* rho, double* u, int where) {
     if (!rho && !u) return CMLBM_OK;
     DeviceGuard g(h->cfg.device);
     if (where == CMLBM_DEVICE) return cmlbm_moments_of(h, h->buf[h->cur], rho, u);
+    double* mrho = (double*)mapped_host(rho);
+    double* mu = (double*)mapped_host(u);
+    if ((!rho || mrho) && (!u || mu)) {
+        // page-locked outputs: the moments kernel writes them in place
+        cudaError_t e = do_moments(h, h->buf[h->cur], mrho, mu);
+        if (e != cudaSuccess) return cuda_fail(h, e, "moments kernel");
+        e = cudaStreamSynchronize(h->st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "moments");
+        return CMLBM_OK;
+    }
     int rc = ensure_stage(h);
     if (rc) return rc;
     const size_t N = (size_t)h->p.N;
