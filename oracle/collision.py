@@ -146,10 +146,11 @@ def _factorized_attractor(kM, post2, rho, lat):
     off-diagonal k~_de, any other pattern gives 0; k factors are divided by rho^(k-1).
     Second order keeps the Maxwellian attractor.
 
-    Parity unpinned for the 3D rules: the paper gives the factorized attractor for D2Q9 only.
-    The D2Q9 form is pinned against the printed element-wise kernel (``literal.py``); the 3D
-    products are pinned only by the property that they reduce to the Maxwellian attractor when
-    the second-order moments are at equilibrium.
+    Parity unpinned for the 3D rules of the moments with a z exponent: the paper gives the
+    factorized attractor for D2Q9 only. The D2Q9 form is pinned against the printed element-wise
+    kernel (``literal.py``). The 3D rules of the moments without a z exponent are pinned to it:
+    a one-cell-thick D3Q27 run of a 2D flow reproduces the D2Q9 run. All 3D products reduce to
+    the Maxwellian attractor when the second-order moments are at equilibrium.
     """
     idx = {a: k for k, a in enumerate(lat.monomials)}
     out = kM.clone()

@@ -5,7 +5,8 @@ The mistakes are the ones a restatement of the paper could plausibly make: a dro
 sign-flipped F/2 in the velocity, a source without its sigma/2 feedback or with the wrong
 factor, a wrong Maxwellian moment, central moments about the wrong velocity, a transposed
 stream, swapped third/fourth-order rates, a wrong eddy-viscosity
-constant, a flipped moving-wall term, and an initial state without its -S/2 term.
+constant, a flipped moving-wall term, an initial state without its -S/2 term, and a 3D
+factorized attractor built over the wrong axes.
 """
 import inspect
 import os
@@ -115,7 +116,19 @@ MUTATIONS = {
         mp, ST, "_wall_terms",
         lambda f: lambda lat, i, shape, bc, uw, sign: (lambda m, w: (m, -w))(*f(lat, i, shape, bc, uw, sign))),
     "initial state without -S/2": lambda mp: _wrap(mp, C, "equilibrium", lambda f: lambda rho, u, F, lat: f(rho, u, 0 * F, lat)),
+    "factorized fourth order over the wrong axes": lambda mp: _wrap(mp, C, "_factorized_attractor", _swap_xxyy),
 }
+
+
+def _swap_xxyy(f):
+    """The factorized attractor of (2, 2, 0) built from k~_xx k~_zz instead of k~_xx k~_yy."""
+    def g(kM, post2, rho, lat):
+        out = f(kM, post2, rho, lat)
+        idx = {a: k for k, a in enumerate(lat.monomials)}
+        if (2, 2, 0) in idx and (0, 0, 2) in idx:
+            out[idx[(2, 2, 0)]] = post2[idx[(2, 0, 0)]] * post2[idx[(0, 0, 2)]] / rho
+        return out
+    return g
 
 
 @pytest.mark.parametrize("name", list(MUTATIONS))
