@@ -146,11 +146,13 @@ def _factorized_attractor(kM, post2, rho, lat):
     off-diagonal k~_de, any other pattern gives 0; k factors are divided by rho^(k-1).
     Second order keeps the Maxwellian attractor.
 
-    Parity unpinned for the 3D rules of the moments with a z exponent: the paper gives the
-    factorized attractor for D2Q9 only. The D2Q9 form is pinned against the printed element-wise
-    kernel (``literal.py``). The 3D rules of the moments without a z exponent are pinned to it:
-    a one-cell-thick D3Q27 run of a 2D flow reproduces the D2Q9 run. All 3D products reduce to
-    the Maxwellian attractor when the second-order moments are at equilibrium.
+    The paper gives the factorized attractor for D2Q9 only. The D2Q9 form is pinned against the
+    printed element-wise kernel (``literal.py``). The 3D rules of every moment with at most two
+    non-zero exponents are pinned to it: a one-cell-thick D3Q27 run of a 2D flow in the x-y,
+    x-z or y-z plane reproduces the D2Q9 run. Parity unpinned for the moments with three
+    non-zero exponents ((1,1,1), (2,1,1) and its permutations, (2,2,1) and its permutations,
+    (2,2,2)): they are pinned only by reducing to the Maxwellian attractor when the second-order
+    moments are at equilibrium.
     """
     idx = {a: k for k, a in enumerate(lat.monomials)}
     out = kM.clone()

@@ -176,3 +176,41 @@ def test_galilean_invariance_of_taylor_green_decay():
         E.append(np.array(out))
     E0 = E[0][0]
     assert np.abs(E[0] - E[1]).max() / E0 < 4e-3
+
+
+@pytest.mark.parametrize("plane", ["xz", "yz"])
+@pytest.mark.parametrize("attractor", ["maxwell", "factorized"])
+def test_d3q27_one_cell_thick_in_other_planes_reproduces_d2q9(plane, attractor):
+    """The same reduction with the flow in the x-z or y-z plane (one cell along the third axis):
+    the D2Q9 axes (x, y) map to (x, z) or (y, z). With the factorized attractor this pins the
+    3D rules of the (a, 0, c) and (0, b, c) moment families to the D2Q9 form as well."""
+    N = 10
+    rho, u = W.taylor_green(N, N, 1, u0=0.03, background=(0.01, -0.02, 0.0), two_d=True)
+    F = W.gaussian_force(N, N, 1, seed=5, std=1e-4)
+    p = Params(tau=0.68, omega3=1.15, omega4=0.85, attractor=attractor)
+    a = OracleSim("D2Q9", N, N, 1, p)
+    a.set_force(field=torch.tensor(np.stack([F[0], F[1], 0 * F[2]])))
+    a.init(torch.tensor(rho), torch.tensor(u))
+    # 2D arrays are [1, y, x]; the D3Q27 box is [z, 1, x] (plane xz) or [z, y, 1] (plane yz)
+    if plane == "xz":
+        shape3, axes = (N, 1, N), (0, 2)
+        to3 = lambda f: f[0][:, None, :]
+    else:
+        shape3, axes = (N, N, 1), (1, 2)
+        to3 = lambda f: f[0][:, :, None]
+    nz3, ny3, nx3 = shape3
+    u3 = np.zeros((3,) + shape3)
+    F3 = np.zeros((3,) + shape3)
+    for k, d in enumerate(axes):
+        u3[d] = to3(u[k])
+        F3[d] = to3(F[k])
+    b = OracleSim("D3Q27", nx3, ny3, nz3, p)
+    b.set_force(field=torch.tensor(F3))
+    b.init(torch.tensor(to3(rho)), torch.tensor(u3))
+    a.step(15)
+    b.step(15)
+    ra, ua = a.moments()
+    rb, ub = b.moments()
+    assert (torch.tensor(to3(ra.numpy())) - rb).abs().max().item() < 1e-14
+    for k, d in enumerate(axes):
+        assert (torch.tensor(to3(ua[k].numpy())) - ub[d]).abs().max().item() < 1e-14

@@ -116,19 +116,25 @@ MUTATIONS = {
         mp, ST, "_wall_terms",
         lambda f: lambda lat, i, shape, bc, uw, sign: (lambda m, w: (m, -w))(*f(lat, i, shape, bc, uw, sign))),
     "initial state without -S/2": lambda mp: _wrap(mp, C, "equilibrium", lambda f: lambda rho, u, F, lat: f(rho, u, 0 * F, lat)),
-    "factorized fourth order over the wrong axes": lambda mp: _wrap(mp, C, "_factorized_attractor", _swap_xxyy),
+    "factorized (2,2,0) over the wrong axes": lambda mp: _wrap(mp, C, "_factorized_attractor",
+                                                              _wrong_axes((2, 2, 0), (2, 0, 0), (0, 0, 2))),
+    "factorized (2,0,2) over the wrong axes": lambda mp: _wrap(mp, C, "_factorized_attractor",
+                                                              _wrong_axes((2, 0, 2), (2, 0, 0), (0, 2, 0))),
 }
 
 
-def _swap_xxyy(f):
-    """The factorized attractor of (2, 2, 0) built from k~_xx k~_zz instead of k~_xx k~_yy."""
-    def g(kM, post2, rho, lat):
-        out = f(kM, post2, rho, lat)
-        idx = {a: k for k, a in enumerate(lat.monomials)}
-        if (2, 2, 0) in idx and (0, 0, 2) in idx:
-            out[idx[(2, 2, 0)]] = post2[idx[(2, 0, 0)]] * post2[idx[(0, 0, 2)]] / rho
-        return out
-    return g
+def _wrong_axes(target, m1, m2):
+    """The factorized attractor of `target` built from the relaxed second-order moments m1, m2
+    of the wrong pair of axes."""
+    def make(f):
+        def g(kM, post2, rho, lat):
+            out = f(kM, post2, rho, lat)
+            idx = {a: k for k, a in enumerate(lat.monomials)}
+            if target in idx and m1 in idx and m2 in idx:
+                out[idx[target]] = post2[idx[m1]] * post2[idx[m2]] / rho
+            return out
+        return g
+    return make
 
 
 @pytest.mark.parametrize("name", list(MUTATIONS))
