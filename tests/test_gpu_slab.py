@@ -201,9 +201,10 @@ def test_slab_only_calls_are_rejected(cm):
     s.close()
 
 
-@pytest.mark.parametrize("storage", ["f32", "bf16"])
-def test_slabs_with_the_two_cell_kernel(cm, storage):
-    """The packed two-cells-per-thread step on slabs against the same kernel on one domain."""
+@pytest.mark.parametrize("storage,force", [("f32", 0.0), ("bf16", 0.0), ("f32", 1e-5)])
+def test_slabs_with_the_two_cell_kernel(cm, storage, force):
+    """The packed two-cells-per-thread step on slabs against the same kernel on one domain
+    (unforced FP32: cells x, x + nx/2 per thread; 16-bit or forced: adjacent cells)."""
     nx, ny, nz = 64, 6, 9
     g = np.random.default_rng(11)
     rho = 1.0 + 0.01 * g.standard_normal((nz, ny, nx))
@@ -211,10 +212,12 @@ def test_slabs_with_the_two_cell_kernel(cm, storage):
     kw = dict(lattice="D3Q27", nx=nx, ny=ny, storage=storage, tau=0.53, omega_bulk=1.0, smagorinsky_cs=0.1,
               kernel="pair")
     ref = cm.Solver(nz=nz, bc=("periodic", "bounceback", "periodic"), **kw)
+    ref.set_force((force, 0.0, 0.0))
     ref.init(torch.tensor(rho, device="cuda"), torch.tensor(u, device="cuda"))
     slabs = []
     for r in range(2):
         s, z0 = SL.cuda_slab(cm, nz, r, 2, bc=("periodic", "bounceback"), **kw)
+        s.set_force((force, 0.0, 0.0))
         sl = slice(z0, z0 + s.shape[0])
         s.init(torch.tensor(rho[sl], device="cuda"), torch.tensor(u[:, sl], device="cuda"))
         slabs.append(s)
