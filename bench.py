@@ -581,6 +581,19 @@ def our_arm(args, dist):
                 forms["adjoint128_f32"] = rollout.benchmark(cm, n=128, steps=100, segment=50)
             except Exception as e:  # noqa: BLE001
                 forms["adjoint128_f32"] = {"error": str(e)[:200]}
+        # the 16-bit and adjoint forms against the plain FP32 step of the same flow on this GPU
+        if args.storage == "f32" and not hit:
+            for k in (f"tgv{n}_bf16", f"tgv{n}_f16"):
+                if "MLUPS" in forms.get(k, {}):
+                    forms[k]["vs_fp32_step"] = forms[k]["MLUPS"] / value
+        h32 = forms.get("hit512_les_f32", {}).get("MLUPS")
+        for k in ("hit512_les_bf16", "hit512_les_f16"):
+            if h32 and "MLUPS" in forms.get(k, {}):
+                forms[k]["vs_fp32_step"] = forms[k]["MLUPS"] / h32
+        adj = forms.get("adjoint128_f32", {})
+        if "forward_MLUPS" in adj:
+            adj["backward_vs_forward"] = adj["backward_MLUPS"] / adj["forward_MLUPS"]
+            adj["fwd_plus_adjoint_vs_forward"] = adj["fwd_plus_adjoint_MLUPS"] / adj["forward_MLUPS"]
         line["forms"] = forms
         if not args.no_cpu:
             line["cpu_baseline"] = cpu_baseline()
