@@ -130,9 +130,13 @@ template <class R> using scalar_t = typename Scalar<R>::T;
 // Params at run time. SIMPLE: no force anywhere (sigma = 0 at every order) and
 // omega_3 = omega_4 = 1, so every moment of order >= 3 leaves the collision at its attractor
 // and the pre-collision moments of those orders are never needed (the compiler drops them).
-template <bool WALLS_, bool LES_, bool FIELD_, bool GEN_, bool SIMPLE_ = false> struct Feat {
-    static constexpr bool WALLS = WALLS_, LES = LES_, FIELD = FIELD_, GEN = GEN_, SIMPLE = SIMPLE_;
+// UNIT: a forced flow with omega_3 = omega_4 = 1, so that every moment of order >= 3 leaves the
+// collision as its attractor plus the source term (the same values the general relaxation
+// gives at unit rates, with its multiplications by 1 - omega and omega left out).
+template <bool WALLS_, bool LES_, bool FIELD_, bool GEN_, bool SIMPLE_ = false, bool UNIT_ = false> struct Feat {
+    static constexpr bool WALLS = WALLS_, LES = LES_, FIELD = FIELD_, GEN = GEN_, SIMPLE = SIMPLE_, UNIT = UNIT_;
     static_assert(!SIMPLE_ || (!FIELD_ && !GEN_), "SIMPLE excludes force fields and the general forms");
+    static_assert(!UNIT_ || (!SIMPLE_ && !GEN_), "UNIT is the forced standard collision");
 };
 
 // ------------------------------------------------------------------------------------------
@@ -705,9 +709,13 @@ __device__ __forceinline__ void collide(R (&m)[Lat<D>::Q], const R F[3], const P
                             DM = fma(Toff, fma(Tdg, irho, third), -((third + q[dtwo]) * uoff));
                         }
                     }
-                    const R w = (ord(t) == 3) ? w3 : w4;
-                    const R om = (ord(t) == 3) ? om3 : om4;
-                    m[t] = fma(om, m[t] + hs, fma(w, DM, hs));
+                    if constexpr (FT::UNIT) {
+                        m[t] = DM + hs;      // fma(0, ., fma(1, DM, hs)) of the general form
+                    } else {
+                        const R w = (ord(t) == 3) ? w3 : w4;
+                        const R om = (ord(t) == 3) ? om3 : om4;
+                        m[t] = fma(om, m[t] + hs, fma(w, DM, hs));
+                    }
                 }
             });
         });

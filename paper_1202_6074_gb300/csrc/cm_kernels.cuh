@@ -202,7 +202,11 @@ inline bool has_walls(const Params& p) { return p.bc[0] == 1 || p.bc[1] == 1 || 
 template <int D, class S, class FT>
 void launch_step_ft(const void* src, void* dst, const void* Ff, const Params& p, cudaStream_t st) {
     using R = typename Codec<S>::R;
-    if constexpr (D == 3 && sizeof(R) == 4) {
+    if constexpr (FT::UNIT) {           // only dispatched to the two-cells-per-thread kernel
+        static_assert(D == 3 && sizeof(R) == 4, "UNIT variants are pair-kernel variants");
+        launch_pair<S, FT>(src, dst, Ff, p, st);
+        return;
+    } else if constexpr (D == 3 && sizeof(R) == 4) {
         if (p.pair) {
             launch_pair<S, FT>(src, dst, Ff, p, st);
             return;
@@ -228,6 +232,13 @@ void launch_step_g(const void* src, void* dst, const void* Ff, const Params& p, 
     if constexpr (!F) {
         if (simple_collision(p)) {
             launch_step_ft<D, S, Feat<W, L, false, false, true>>(src, dst, Ff, p, st);
+            return;
+        }
+    }
+    using R = typename Codec<S>::R;
+    if constexpr (D == 3 && sizeof(R) == 4) {
+        if (p.pair && p.omega3 == 1.0 && p.omega4 == 1.0) {
+            launch_step_ft<D, S, Feat<W, L, F, false, false, true>>(src, dst, Ff, p, st);
             return;
         }
     }

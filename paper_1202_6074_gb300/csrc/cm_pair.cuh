@@ -15,15 +15,16 @@ namespace cm {
 // Resident blocks per SM the register budget is sized for. The 16-bit steps are bound by
 // instruction latency rather than by HBM and gain from more resident warps where the registers
 // allow: 6 blocks (at most 80 registers, a 4-byte spill) for the unforced SIMPLE collision,
-// +2 %; 5 (at most 96, an 84-byte spill) for forced steps without a force field, +5 % on the
-// channel. A force field (the isotropic turbulence LES) loses 1 % at 5 blocks and stays at 4
-// (at most 128 registers), as do the general forms (they spill twice as much at 5) and all
-// FP32 steps (the forced FP32 LES loses 7 % at 5).
+// +2 %; 5 (at most 96) for forced steps without a force field (+5 % on the channel) and for
+// the UNIT collision with a force field (+1.6 % on the isotropic turbulence LES). The general
+// relaxation with a force field loses 1 % at 5 blocks and stays at 4 (at most 128 registers),
+// as do the general forms (they spill twice as much at 5) and all FP32 steps (the forced FP32
+// LES loses 7 % at 5).
 template <class S, class FT>
 constexpr int pair_min_blocks() {
     if constexpr (sizeof(S) == 2)
         return FT::SIMPLE ? CM_PAIR_MIN_BLOCKS + 2
-                          : (!FT::FIELD && !FT::GEN ? CM_PAIR_MIN_BLOCKS + 1 : CM_PAIR_MIN_BLOCKS);
+                          : ((!FT::FIELD && !FT::GEN) || FT::UNIT ? CM_PAIR_MIN_BLOCKS + 1 : CM_PAIR_MIN_BLOCKS);
     return CM_PAIR_MIN_BLOCKS;
 }
 
@@ -324,6 +325,17 @@ int launch_pair_two_steps(const void* A, void* C, void* ring, int P, int slots, 
     template void launch_pair<S, Feat<false, true, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);  \
     template void launch_pair<S, Feat<true, false, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);  \
     template void launch_pair<S, Feat<true, true, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);
+
+// the forced standard collision with unit higher-order rates (the default rates)
+#define CM_PAIR_INSTANTIATE_UNIT(S)                                                                         \
+    template void launch_pair<S, Feat<false, false, false, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t); \
+    template void launch_pair<S, Feat<false, false, true, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);  \
+    template void launch_pair<S, Feat<false, true, false, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);  \
+    template void launch_pair<S, Feat<false, true, true, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);   \
+    template void launch_pair<S, Feat<true, false, false, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);  \
+    template void launch_pair<S, Feat<true, false, true, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);   \
+    template void launch_pair<S, Feat<true, true, false, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);   \
+    template void launch_pair<S, Feat<true, true, true, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);
 
 // the general forms (factorized attractor, reduced compressibility), in translation units of
 // their own so that the library builds in parallel
