@@ -132,11 +132,12 @@ template <class R> using scalar_t = typename Scalar<R>::T;
 // and the pre-collision moments of those orders are never needed (the compiler drops them).
 // UNIT: a forced flow with omega_3 = omega_4 = 1, so that every moment of order >= 3 leaves the
 // collision as its attractor plus the source term (the same values the general relaxation
-// gives at unit rates, with its multiplications by 1 - omega and omega left out).
+// gives at unit rates, with its multiplications by 1 - omega and omega left out); with GEN the
+// attractor is the factorized one where the parameters select it.
 template <bool WALLS_, bool LES_, bool FIELD_, bool GEN_, bool SIMPLE_ = false, bool UNIT_ = false> struct Feat {
     static constexpr bool WALLS = WALLS_, LES = LES_, FIELD = FIELD_, GEN = GEN_, SIMPLE = SIMPLE_, UNIT = UNIT_;
     static_assert(!SIMPLE_ || (!FIELD_ && !GEN_), "SIMPLE excludes force fields and the general forms");
-    static_assert(!UNIT_ || (!SIMPLE_ && !GEN_), "UNIT is the forced standard collision");
+    static_assert(!UNIT_ || !SIMPLE_, "UNIT is a forced collision");
 };
 
 // ------------------------------------------------------------------------------------------

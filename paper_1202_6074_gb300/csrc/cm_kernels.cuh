@@ -225,7 +225,14 @@ inline bool simple_collision(const Params& p) {
 
 template <int D, class S, bool W, bool L, bool F>
 void launch_step_g(const void* src, void* dst, const void* Ff, const Params& p, cudaStream_t st) {
+    using R = typename Codec<S>::R;
     if (p.attractor != 0 || p.reduced) {
+        if constexpr (D == 3 && sizeof(R) == 4) {
+            if (p.pair && p.omega3 == 1.0 && p.omega4 == 1.0) {
+                launch_step_ft<D, S, Feat<W, L, F, true, false, true>>(src, dst, Ff, p, st);
+                return;
+            }
+        }
         launch_step_ft<D, S, Feat<W, L, F, true>>(src, dst, Ff, p, st);
         return;
     }
@@ -235,7 +242,6 @@ void launch_step_g(const void* src, void* dst, const void* Ff, const Params& p, 
             return;
         }
     }
-    using R = typename Codec<S>::R;
     if constexpr (D == 3 && sizeof(R) == 4) {
         if (p.pair && p.omega3 == 1.0 && p.omega4 == 1.0) {
             launch_step_ft<D, S, Feat<W, L, F, false, false, true>>(src, dst, Ff, p, st);

@@ -24,7 +24,7 @@ template <class S, class FT>
 constexpr int pair_min_blocks() {
     if constexpr (sizeof(S) == 2)
         return FT::SIMPLE ? CM_PAIR_MIN_BLOCKS + 2
-                          : ((!FT::FIELD && !FT::GEN) || FT::UNIT ? CM_PAIR_MIN_BLOCKS + 1 : CM_PAIR_MIN_BLOCKS);
+                          : (!FT::GEN && (!FT::FIELD || FT::UNIT) ? CM_PAIR_MIN_BLOCKS + 1 : CM_PAIR_MIN_BLOCKS);
     return CM_PAIR_MIN_BLOCKS;
 }
 
@@ -336,6 +336,17 @@ int launch_pair_two_steps(const void* A, void* C, void* ring, int P, int slots, 
     template void launch_pair<S, Feat<true, false, true, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);   \
     template void launch_pair<S, Feat<true, true, false, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);   \
     template void launch_pair<S, Feat<true, true, true, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);
+
+// the general forms with unit higher-order rates
+#define CM_PAIR_INSTANTIATE_GEN_UNIT(S)                                                                     \
+    template void launch_pair<S, Feat<false, false, false, true, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t); \
+    template void launch_pair<S, Feat<false, false, true, true, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);  \
+    template void launch_pair<S, Feat<false, true, false, true, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);  \
+    template void launch_pair<S, Feat<false, true, true, true, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);   \
+    template void launch_pair<S, Feat<true, false, false, true, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);  \
+    template void launch_pair<S, Feat<true, false, true, true, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);   \
+    template void launch_pair<S, Feat<true, true, false, true, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);   \
+    template void launch_pair<S, Feat<true, true, true, true, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);
 
 // the general forms (factorized attractor, reduced compressibility), in translation units of
 // their own so that the library builds in parallel
