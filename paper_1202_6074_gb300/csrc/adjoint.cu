@@ -144,8 +144,9 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_terminal(const S* __restrict
 }
 
 // 5 resident blocks of 128 threads (at most 102 registers, a 64-byte spill) with the L2
-// prefetch below measured fastest at 128^3 and 256^3: 14.0 G cells/s at 256^3, against 13.4
-// with 4 blocks (no spill) and 9.5 with neither the prefetch nor the fifth block
+// prefetch below measured fastest at 128^3 and 256^3: 14.0 G cells/s at 256^3 (14.2 with the
+// unit-rate variant), against 13.4 with 4 blocks (no spill) and 9.5 with neither the prefetch
+// nor the fifth block
 #ifndef CM_ADJ_MIN_BLOCKS
 #define CM_ADJ_MIN_BLOCKS 5
 #endif
@@ -154,7 +155,9 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_terminal(const S* __restrict
 #endif
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
-template <int D, class S, bool WALLS>
+// UNIT: omega_3 = omega_4 = 1 (the default rates), so that the post-collision moments of order
+// >= 3 are kappa^M + sigma / 2 and their adjoints need neither rate (fewer live registers)
+template <int D, class S, bool WALLS, bool UNIT = false>
 __global__ void __launch_bounds__(kBlock, CM_ADJ_MIN_BLOCKS) k_adjoint_step(const S* __restrict__ state, const typename Codec<S>::R* __restrict__ Ff,
                                                         PR<typename Codec<S>::R> p, const typename Codec<S>::R* __restrict__ lam_in,
                                                         typename Codec<S>::R* __restrict__ lam_out, double* __restrict__ dLdF) {
@@ -223,8 +226,12 @@ __global__ void __launch_bounds__(kBlock, CM_ADJ_MIN_BLOCKS) k_adjoint_step(cons
                 K[t] = A[t] + R(0.5) * s;
                 constexpr bool even = (a % 2 == 0) && (b % 2 == 0) && (c % 2 == 0);
                 constexpr R cM = even ? (R)third_pow((a == 2) + (b == 2) + (c == 2)) : R(0);
-                const R w = (n == 3) ? w3 : w4;
-                B[t] = (R(1) - w) * A[t] + w * cM * rho + (R(1) - R(0.5) * w) * s;
+                if constexpr (UNIT) {
+                    B[t] = cM * rho + R(0.5) * s;
+                } else {
+                    const R w = (n == 3) ? w3 : w4;
+                    B[t] = (R(1) - w) * A[t] + w * cM * rho + (R(1) - R(0.5) * w) * s;
+                }
             }
         });
     });
@@ -279,14 +286,21 @@ __global__ void __launch_bounds__(kBlock, CM_ADJ_MIN_BLOCKS) k_adjoint_step(cons
             if constexpr (n >= 3 && ord(t) == n) {
                 constexpr int a = ex_a(t), b = ex_b(t), c = ex_c(t);
                 constexpr bool even = (a % 2 == 0) && (b % 2 == 0) && (c % 2 == 0);
-                const R w = (n == 3) ? w3 : w4;
                 const R pb = L[t];
-                const R sb = fma((n == 3) ? hw3 : hw4, pb, R(0.5) * B[t]);
-                if constexpr (even) {
-                    constexpr R cM = (R)third_pow((a == 2) + (b == 2) + (c == 2));
-                    rb = fma(w * cM, pb, rb);
+                R sb;
+                if constexpr (UNIT) {
+                    sb = R(0.5) * (pb + B[t]);
+                    if constexpr (even) rb = fma((R)third_pow((a == 2) + (b == 2) + (c == 2)), pb, rb);
+                    L[t] = B[t];                                   // kbarbar
+                } else {
+                    const R w = (n == 3) ? w3 : w4;
+                    sb = fma((n == 3) ? hw3 : hw4, pb, R(0.5) * B[t]);
+                    if constexpr (even) {
+                        constexpr R cM = (R)third_pow((a == 2) + (b == 2) + (c == 2));
+                        rb = fma(w * cM, pb, rb);
+                    }
+                    L[t] = fma((n == 3) ? om3 : om4, pb, B[t]);   // kbarbar
                 }
-                L[t] = fma((n == 3) ? om3 : om4, pb, B[t]);       // kbarbar
                 if constexpr (a == 1) G1[0] = fma(K[t - 1], sb, G1[0]);
                 if constexpr (a == 2) G2[0] = fma(K[t - 1], sb, G2[0]);
                 if constexpr (a > 0) B[t - 1] = fma(aFr[a - 1][0], sb, B[t - 1]);
@@ -390,10 +404,15 @@ template <int D, class R>
 cudaError_t launch_adjoint_step(const void* state, const void* Ff, const Params& p, const void* lam_in, void* lam_out,
                                 double* dLdF, cudaStream_t st) {
     const dim3 b = cell_block(p.nx), g = cell_grid(p, b);
-    if (has_walls(p))
-        k_adjoint_step<D, R, true><<<g, b, 0, st>>>((const R*)state, (const R*)Ff, typed<R>(p), (const R*)lam_in, (R*)lam_out, dLdF);
-    else
-        k_adjoint_step<D, R, false><<<g, b, 0, st>>>((const R*)state, (const R*)Ff, typed<R>(p), (const R*)lam_in, (R*)lam_out, dLdF);
+    const bool unit = p.omega3 == 1.0 && p.omega4 == 1.0;
+    auto go = [&](auto walls, auto u) {
+        k_adjoint_step<D, R, decltype(walls)::value, decltype(u)::value><<<g, b, 0, st>>>(
+            (const R*)state, (const R*)Ff, typed<R>(p), (const R*)lam_in, (R*)lam_out, dLdF);
+    };
+    using T_ = std::true_type;
+    using F_ = std::false_type;
+    if (has_walls(p)) unit ? go(T_{}, T_{}) : go(T_{}, F_{});
+    else unit ? go(F_{}, T_{}) : go(F_{}, F_{});
     return cudaGetLastError();
 }
 
