@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--form-steps", type=int, default=40)
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"],
                     help="population storage of the timed step (f32 is the headline)")
+    ap.add_argument("--no-cpu-samples", action="store_true",
+                    help="skip the oracle timings on reduced samples of the other workloads (about 15 s "
+                         "of host-core work)")
     ap.add_argument("--flow", default="tgv", choices=["tgv", "hit"],
                     help="timed workload: the Taylor-Green vortex (headline) or the forced isotropic "
                          "turbulence LES (force field, Cs = 0.1) on the same n^3 box")
@@ -434,6 +437,58 @@ def cpu_baseline(n=64, steps=50, n1=40, steps1=4):
             "one_core": {"value": v1, "sample": f"{n1}^3 x {steps1} steps", "seconds": sec1}}
 
 
+def cpu_samples():
+    """The FP64 oracle on reduced samples of the other workloads (host cores, MLUPS each): the
+    D2Q9 body-force channel (1000 of its 5000 steps), the forced isotropic LES and the wall-bounded
+    channel LES on small boxes, and the adjoint (forward + reverse by automatic differentiation
+    through the oracle) on a 16^3 box."""
+    from oracle import adjoint as A
+    from oracle.solver import OracleSim
+    from oracle.collision import Params
+    from paper_1202_6074_gb300 import workloads as W
+
+    out = {}
+
+    def timed(name, sample, cells, steps, fn):
+        t0 = time.perf_counter()
+        fn()
+        sec = time.perf_counter() - t0
+        out[name] = {"MLUPS": cells * steps / sec / 1e6, "sample": sample, "seconds": sec}
+
+    o = OracleSim("D2Q9", 64, 32, 1, Params(tau=0.8), bc=("periodic", "bounceback", "periodic"))
+    o.set_force((1e-6, 0.0, 0.0))
+    o.init(None, None)
+    timed("d2q9_poiseuille64x32", "64x32 x 1000 steps", 64 * 32, 1000, lambda: o.step(1000))
+
+    n = 32
+    o = OracleSim("D3Q27", n, n, n, Params(tau=HIT_TAU, cs_smag=0.1))
+    o.set_force(field=torch.tensor(W.hit_forcing(n, n, n, seed=1)))
+    o.init(None, None)
+    timed("hit_les", f"{n}^3 x 10 steps, force field, Smagorinsky", n ** 3, 10, lambda: o.step(10))
+
+    nx, ny, nz = 64, 32, 16
+    rho, u, F = W.channel(nx, ny, nz, seed=5)
+    o = OracleSim("D3Q27", nx, ny, nz, Params(tau=0.51067, cs_smag=0.1), bc=("periodic", "bounceback", "periodic"),
+                  van_driest=(26.0, 0.005 / ((0.51067 - 0.5) / 3)))
+    o.set_force((1.953e-7, 0.0, 0.0))
+    o.init(torch.tensor(rho), torch.tensor(u))
+    timed("channel_les", f"{nx}x{ny}x{nz} x 10 steps, walls, Smagorinsky + van Driest", nx * ny * nz, 10,
+          lambda: o.step(10))
+
+    n = 16
+    p = Params(tau=0.6)
+    rho, u0 = W.random_solenoidal(n, n, n, seed=2, u_rms=0.02)
+    F = torch.tensor(W.gaussian_force(n, n, n, seed=3, std=1e-5))
+    sim = OracleSim("D3Q27", n, n, n, p)
+    sim.set_force(field=F)
+    sim.init(torch.tensor(rho), torch.tensor(u0))
+    s0 = sim.s.clone()
+    target = torch.zeros((3, n, n, n), dtype=torch.float64)
+    timed("adjoint", f"{n}^3 x 10 steps forward + reverse", n ** 3, 10,
+          lambda: A.loss_and_grad(("D3Q27", n, n, n, p), s0, F, target, 10))
+    return out
+
+
 # ------------------------------------------------------------------------------------------
 # arms
 # ------------------------------------------------------------------------------------------
@@ -597,6 +652,8 @@ def our_arm(args, dist):
         line["forms"] = forms
         if not args.no_cpu:
             line["cpu_baseline"] = cpu_baseline()
+            if not args.no_cpu_samples:
+                line["cpu_baseline"]["other_workloads"] = cpu_samples()
         print(json.dumps(line))
 
 

@@ -27,4 +27,4 @@ def loss_and_grad(sim_args, s0, F, target, steps, sim_kwargs=None):
     L = velocity_loss(sim_args, torch.as_tensor(s0, dtype=DT).detach(), Fp, torch.as_tensor(target, dtype=DT),
                       steps, sim_kwargs)
     L.backward()
-    return float(L), Fp.grad.detach()
+    return float(L.detach()), Fp.grad.detach()
