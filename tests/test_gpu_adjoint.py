@@ -37,10 +37,11 @@ CASES = {
 }
 
 
-def _setup(cm, case, storage, steps_kw=None):
+def _setup(cm, case, storage, steps_kw=None, unit_rates=False):
     nz, ny, nx = case["shape"]
     lat = case["lattice"]
-    p = dict(tau=0.6, omega_3=1.1, omega_4=0.9)
+    # unit higher-order rates select the adjoint's unit-rate kernel variant
+    p = dict(tau=0.6, omega_3=1.0, omega_4=1.0) if unit_rates else dict(tau=0.6, omega_3=1.1, omega_4=0.9)
     rho, u = W.random_solenoidal(nx, ny, nz, seed=2, u_rms=0.03)
     F = W.gaussian_force(nx, ny, nz, seed=3, std=1e-3)
     target = W.gaussian_force(nx, ny, nz, seed=4, std=1e-2)
@@ -72,13 +73,14 @@ def _gpu_grad(rollout, s, s0, F, target, steps, segment):
     return float(L), Fp.grad.detach().cpu()
 
 
+@pytest.mark.parametrize("unit_rates", [False, True])
 @pytest.mark.parametrize("storage,tol", [("f64", 1e-10), ("f32", 1e-4)])
 @pytest.mark.parametrize("name", list(CASES))
-def test_adjoint_matches_oracle_gradient(mods, name, storage, tol):
+def test_adjoint_matches_oracle_gradient(mods, name, storage, tol, unit_rates):
     cm, rollout = mods
     case = CASES[name]
     steps = 6
-    s, s0, F, target, uw, p = _setup(cm, case, storage)
+    s, s0, F, target, uw, p = _setup(cm, case, storage, unit_rates=unit_rates)
     Lg, gg = _gpu_grad(rollout, s, s0, F, target, steps, segment=4)
     Lo, go = _oracle_grad(case, s0, F, target, uw, p, steps)
     assert abs(Lg - Lo) <= 1e-12 + (1e-12 if storage == "f64" else 1e-6) * abs(Lo)
