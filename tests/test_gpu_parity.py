@@ -395,6 +395,8 @@ def test_tma_requested_on_ineligible_config_is_rejected(cm):
 PAIR_CASES = {
     "pair_factorized_field": dict(lattice="D3Q27", shape=(5, 6, 64), flow="tgv",
                                   kw=dict(tau=0.58, omega_3=1.1, omega_4=1.3, attractor="factorized")),
+    "pair_field_general_rates": dict(lattice="D3Q27", shape=(5, 5, 64), flow="tgv",
+                                     kw=dict(tau=0.59, omega_3=1.2, omega_4=0.8)),
     "pair_factorized_unit_rates": dict(lattice="D3Q27", shape=(4, 7, 64), flow="tgv",
                                        kw=dict(tau=0.57, attractor="factorized", smagorinsky_cs=0.1)),
     "pair_reduced_walls_les": dict(lattice="D3Q27", shape=(5, 8, 128), flow="channel",
