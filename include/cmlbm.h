@@ -180,7 +180,9 @@ CMLBM_API int cmlbm_step(cmlbm_t* h, int nsteps);
 
 /* One step from the state buffer src into dst (device pointers of cmlbm_state_bytes() each,
  * in the handle's layout, src != dst), with the handle's configuration and force. Used for
- * checkpointed recomputation; the handle's own state is untouched. */
+ * checkpointed recomputation; the handle's own state is untouched. Buffers need the alignment
+ * of one storage element; buffers aligned to two elements (any cudaMalloc allocation) let the
+ * two-cells-per-thread kernel pair adjacent cells, which gives the same bits faster. */
 CMLBM_API int cmlbm_step_buffers(cmlbm_t* h, const void* src, void* dst);
 
 /* Density [N] and velocity [3][N] (FP64) of the current pre-collision field (pull of the
