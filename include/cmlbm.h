@@ -26,6 +26,9 @@
  *   - Calls are asynchronous on the handle's stream, except cmlbm_reduce, cmlbm_create,
  *     cmlbm_destroy and calls with CMLBM_HOST buffers, which synchronise the stream.
  *   - Buffers passed in are owned by the caller and only borrowed for the call.
+ *   - Test hook: with the environment variable CMLBM_TEST_ALLOC_LIMIT set to a byte count,
+ *     every device allocation that grows with the grid (state, staging, force field, scratch)
+ *     and is larger than that count fails with CMLBM_ERR_NOMEM without calling cudaMalloc.
  *   - Grid layout: cell (x, y, z) has linear index c = (z * ny + y) * nx + x; N = nx*ny*nz.
  *     Vector fields are [3][N] (component-major). Populations are [Q][N] (direction-major).
  *   - Direction order. D2Q9 (Sec. 2, Eq. velocityd2q9 with the order of the basis

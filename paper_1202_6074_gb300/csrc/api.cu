@@ -12,6 +12,24 @@
 #include "../../include/cmlbm.h"
 #include "cm_launch.h"
 
+#include <cstdlib>
+
+// Device allocations that grow with the grid (state buffers, host staging, force field,
+// turbulence scratch, the two-steps ring). Test hook: with CMLBM_TEST_ALLOC_LIMIT set to a
+// byte count, any such allocation larger than it fails as if the device were out of memory, so
+// that the CMLBM_ERR_NOMEM paths are tested without exhausting a shared GPU's memory.
+static cudaError_t grid_alloc(void** p, size_t bytes) {
+    if (const char* s = std::getenv("CMLBM_TEST_ALLOC_LIMIT")) {
+        char* end = nullptr;
+        const unsigned long long limit = std::strtoull(s, &end, 10);
+        if (end != s && bytes > limit) {
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
+
 struct cmlbm {
     cmlbm_config cfg;
     cm::Params p;
@@ -197,7 +215,7 @@ cudaError_t do_moments(cmlbm* h, const void* src, double* rho, double* u, int z0
 
 int ensure_stage(cmlbm* h) {
     if (h->stage) return CMLBM_OK;
-    cudaError_t e = cudaMalloc(&h->stage, sizeof(double) * 4 * (size_t)h->p.N);
+    cudaError_t e = grid_alloc((void**)&h->stage, sizeof(double) * 4 * (size_t)h->p.N);
     if (e != cudaSuccess) {
         h->stage = nullptr;
         cudaGetLastError();
@@ -307,7 +325,7 @@ int cmlbm_create(const cmlbm_config* cfg, cmlbm_t** out) {
     }
     const size_t bytes = (size_t)h->Q * (size_t)S * h->esize;
     for (int k = 0; k < 2; ++k) {
-        if (cudaMalloc(&h->buf[k], bytes) != cudaSuccess) {
+        if (grid_alloc(&h->buf[k], bytes) != cudaSuccess) {
             cudaGetLastError();
             cmlbm_destroy(h);
             return fail(nullptr, CMLBM_ERR_NOMEM, "cudaMalloc of the state buffers failed");
@@ -338,8 +356,8 @@ int cmlbm_create(const cmlbm_config* cfg, cmlbm_t** out) {
         if (!cm::pair_eligible(p, h->D, c.storage != CMLBM_F64)) {
             cmlbm_destroy(h);
             return fail(nullptr, CMLBM_ERR_UNSUPPORTED,
-                        "the two-cells-per-thread step needs D3Q27, FP32/BF16/FP16 storage, periodic x, nx a "
-                        "multiple of 64 and the standard collision");
+                        "the two-cells-per-thread step needs D3Q27, FP32/BF16/FP16 storage, periodic x and nx a "
+                        "multiple of 64");
         }
         p.pair = 1;
     }
@@ -422,7 +440,7 @@ int cmlbm_set_force(cmlbm_t* h, const double uniform[3], const double* field, in
     if (where != CMLBM_DEVICE && where != CMLBM_HOST) return fail(h, CMLBM_ERR_INVALID, "bad `where`");
     const long long n = 3 * h->p.N;
     if (!h->force) {
-        if (cudaMalloc(&h->force, h->rsize * (size_t)n) != cudaSuccess) {
+        if (grid_alloc(&h->force, h->rsize * (size_t)n) != cudaSuccess) {
             h->force = nullptr;
             cudaGetLastError();
             return fail(h, CMLBM_ERR_NOMEM, "cudaMalloc of the force field failed");
@@ -511,7 +529,7 @@ int cmlbm_step(cmlbm_t* h, int nsteps) {
     DeviceGuard g(h->cfg.device);
     if (nsteps >= 2 && h->two_steps && !h->ring) {
         const size_t bytes = (size_t)(cm::kTwoStepRing + 2) * h->p.nx * h->p.ny * h->Q * h->esize;
-        if (cudaMalloc(&h->ring, bytes) != cudaSuccess) {
+        if (grid_alloc(&h->ring, bytes) != cudaSuccess) {
             cudaGetLastError();
             h->ring = nullptr;
             h->two_steps = false;      // no room for the ring: single steps
@@ -662,12 +680,12 @@ int cmlbm_turbulence_force(cmlbm_t* h, double cs) {
     DeviceGuard g(h->cfg.device);
     const size_t N = (size_t)h->p.N;
     if (!h->force || !h->p.has_field) drop_graphs(h);   // the steps will read a (new) force field
-    if (!h->force && cudaMalloc(&h->force, h->rsize * 3 * N) != cudaSuccess) {
+    if (!h->force && grid_alloc(&h->force, h->rsize * 3 * N) != cudaSuccess) {
         h->force = nullptr;
         cudaGetLastError();
         return fail(h, CMLBM_ERR_NOMEM, "cudaMalloc of the force field failed");
     }
-    if (!h->turb && cudaMalloc(&h->turb, h->rsize * 10 * N) != cudaSuccess) {
+    if (!h->turb && grid_alloc(&h->turb, h->rsize * 10 * N) != cudaSuccess) {
         h->turb = nullptr;
         cudaGetLastError();
         return fail(h, CMLBM_ERR_NOMEM, "cudaMalloc of the turbulence scratch failed");

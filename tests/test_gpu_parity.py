@@ -668,3 +668,25 @@ def test_host_fields_page_locked_and_pageable_agree(cm):
         s.close()
     assert torch.equal(states[0].view(torch.uint8), states[1].view(torch.uint8))
     assert np.array_equal(fields[0][0], fields[1][0]) and np.array_equal(fields[0][1], fields[1][1])
+
+
+def test_out_of_memory_is_reported_and_the_handle_recovers(cm, monkeypatch):
+    """CMLBM_ERR_NOMEM through the allocation-limit test hook (no shared GPU is driven out of
+    memory): a create that cannot allocate its state fails cleanly, and a handle whose staging
+    allocation fails keeps working once memory is available."""
+    monkeypatch.setenv("CMLBM_TEST_ALLOC_LIMIT", "100000")
+    with pytest.raises(cm.CmlbmError) as e:
+        cm.Solver(lattice="D3Q27", nx=32, ny=32, nz=32, storage="f32", tau=0.6)   # 3.5 MB per buffer
+    assert e.value.code == cm.ERR_NOMEM
+    s = cm.Solver(lattice="D3Q27", nx=8, ny=6, nz=4, storage="f32", tau=0.6)      # 21 kB per buffer
+    rho = 1.0 + 0.01 * np.random.default_rng(1).standard_normal((4, 6, 8))
+    monkeypatch.setenv("CMLBM_TEST_ALLOC_LIMIT", "1000")
+    with pytest.raises(cm.CmlbmError) as e:
+        s.init(rho, None)                        # pageable host data needs the 6 kB staging buffer
+    assert e.value.code == cm.ERR_NOMEM
+    monkeypatch.delenv("CMLBM_TEST_ALLOC_LIMIT")
+    s.init(rho, None)
+    s.step(3)
+    red = s.reduce()
+    assert abs(red[0] - rho.sum()) < 1e-6 * rho.sum()
+    s.close()
