@@ -36,6 +36,13 @@ constexpr int pair_min_blocks() {
 // but -1 % for the unforced FP32 step, which stays on (x, x + nx/2).
 template <class S, class FT> constexpr bool pair_adjacent() { return sizeof(S) == 2 || !FT::SIMPLE; }
 
+// Whether the collision takes and returns the stored deviations with the weights folded into its
+// first and last sweeps (collide<..., DEV>), or multiplies by the weights on the way in and out.
+// Measured at 256^3: +1 % (Taylor-Green BF16/FP16) and +2.4 % (channel BF16) with the folded
+// weights, but -0.7 % with a force field (isotropic LES BF16) and -0.2 % for the unforced FP32
+// step; the FP32 steps and the force-field steps keep the explicit weights.
+template <class S, class FT> __host__ __device__ constexpr bool pair_dev() { return sizeof(S) == 2 && !FT::FIELD; }
+
 // Plane ring of the two-steps-per-pass schedule (launch_pair_two_steps): the intermediate state
 // t+1 lives in a small buffer of z-planes instead of a full state buffer. Plane z sits in slot
 // z for z < 2 (kept until the end of the pass: the periodic wrap reads them last) and in slot
@@ -50,6 +57,8 @@ struct Ring {
     }
 };
 
+// The pair gathers return the stored deviations d (moving-wall term included), not h = w d
+// (see pair_dev).
 // RS / RD: the source / destination state is the ring (else a full buffer with stride p.S)
 template <class S, bool WALLS, bool RS = false>
 __device__ __forceinline__ void gather_pair(const S* __restrict__ src, int x, int y, int z, const PR<float>& p, F2 (&h)[27],
@@ -98,7 +107,6 @@ __device__ __forceinline__ void gather_pair(const S* __restrict__ src, int x, in
     sfor<27>([&](auto I) {
         constexpr int i = decltype(I)::value;
         constexpr int a = Lat<3>::ex(i) + 1, b = Lat<3>::ey(i) + 1, c = Lat<3>::ez(i) + 1;
-        constexpr float w = (float)weight<3>(i);
         const unsigned base = i * PS + row[c][b];
         if constexpr (WALLS) {
             const bool by = yo[b], bz = zo[c];
@@ -112,12 +120,12 @@ __device__ __forceinline__ void gather_pair(const S* __restrict__ src, int x, in
             if constexpr (c != 1) eu += bz ? (float(Lat<3>::ex(i)) * p.uw[2][sz][0] + float(Lat<3>::ey(i)) * p.uw[2][sz][1] + float(Lat<3>::ez(i)) * p.uw[2][sz][2]) : 0.f;
             const int cnt = (int)by + (int)bz;
             const float add = 6.f * eu * (cnt == 2 ? 0.5f : 1.f);
-            h[slot<3>(i)] = F2(da + add, db + add) * F2(w);
+            h[slot<3>(i)] = F2(da + add, db + add);
         } else {
             if constexpr (sizeof(S) == 2)   // 64-bit row pointers (measured faster at 16-bit storage)
-                h[slot<3>(i)] = F2(Codec<S>::ld(src + xa[a] + base), Codec<S>::ld(src + xb[a] + base)) * F2(w);
+                h[slot<3>(i)] = F2(Codec<S>::ld(src + xa[a] + base), Codec<S>::ld(src + xb[a] + base));
             else
-                h[slot<3>(i)] = F2(Codec<S>::ld(src + (base + (unsigned)xa[a])), Codec<S>::ld(src + (base + (unsigned)xb[a]))) * F2(w);
+                h[slot<3>(i)] = F2(Codec<S>::ld(src + (base + (unsigned)xa[a])), Codec<S>::ld(src + (base + (unsigned)xb[a])));
         }
     });
 }
@@ -157,7 +165,6 @@ __device__ __forceinline__ void gather_adj(const S* __restrict__ src, int x0, in
     sfor<27>([&](auto I) {
         constexpr int i = decltype(I)::value;
         constexpr int a = Lat<3>::ex(i) + 1, b = Lat<3>::ey(i) + 1, c = Lat<3>::ez(i) + 1;
-        constexpr float w = (float)weight<3>(i);
         const unsigned base = i * PS + row[c][b];
         if constexpr (WALLS) {
             const bool by = yo[b], bz = zo[c];
@@ -176,12 +183,12 @@ __device__ __forceinline__ void gather_adj(const S* __restrict__ src, int x0, in
             if constexpr (c != 1) eu += bz ? (float(Lat<3>::ex(i)) * p.uw[2][sz][0] + float(Lat<3>::ey(i)) * p.uw[2][sz][1] + float(Lat<3>::ez(i)) * p.uw[2][sz][2]) : 0.f;
             const int cnt = (int)by + (int)bz;
             const float add = 6.f * eu * (cnt == 2 ? 0.5f : 1.f);
-            h[slot<3>(i)] = F2(d.x + add, d.y + add) * F2(w);
+            h[slot<3>(i)] = F2(d.x + add, d.y + add);
         } else if constexpr (a == 1) {
             const float2 d = Codec<S>::ld2(src + x0 + base);
-            h[slot<3>(i)] = F2(d.x, d.y) * F2(w);
+            h[slot<3>(i)] = F2(d.x, d.y);
         } else {
-            h[slot<3>(i)] = F2(Codec<S>::ld(src + c0[a] + base), Codec<S>::ld(src + c1[a] + base)) * F2(w);
+            h[slot<3>(i)] = F2(Codec<S>::ld(src + c0[a] + base), Codec<S>::ld(src + c1[a] + base));
         }
     });
 }
@@ -234,11 +241,17 @@ __global__ void __launch_bounds__(kBlock, pair_min_blocks<S, FT>()) k_step_pair(
 #pragma unroll
         for (int d = 0; d < 3; ++d) F[d] = F2(p.F[d]);
     }
-    collide<3, F2, FT>(h, F, p, smagorinsky_constant<float, FT::LES>(p, y));
+    constexpr bool DEV = pair_dev<S, FT>();
+    if constexpr (!DEV) {
+        sfor<27>([&](auto I) {
+            constexpr int t = decltype(I)::value;
+            h[t] = h[t] * F2((float)weight_slot<3>(t));
+        });
+    }
+    collide<3, F2, FT, DEV>(h, F, p, smagorinsky_constant<float, FT::LES>(p, y));
     sfor<27>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        constexpr float iw = (float)inv_weight<3>(i);
-        const F2 v = h[slot<3>(i)] * F2(iw);
+        const F2 v = DEV ? h[slot<3>(i)] : h[slot<3>(i)] * F2((float)inv_weight<3>(i));
         if constexpr (ADJ) {
             Codec<S>::st2(dst + dA + (size_t)PS * i, v.v.x, v.v.y);
         } else if constexpr (sizeof(S) == 2) {
