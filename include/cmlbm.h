@@ -113,10 +113,12 @@ typedef struct cmlbm cmlbm_t;
  *                         ring of 12 planes meant to stay in L2; FP32 storage, no slab,
  *                         nz >= 16; bitwise the same results, measured slower than PAIR on
  *                         GB300), or CMLBM_KERNEL_TMA (rows staged in shared memory by TMA).
- *                         PAIR covers D3Q27 with FP32 / BF16 / FP16 storage, periodic x, nx a
- *                         multiple of 64, the Maxwellian attractor and standard compressibility;
+ *                         PAIR covers D3Q27 with FP32 / BF16 / FP16 storage, periodic x and nx a
+ *                         multiple of 64, in every collision form (PAIR_TWO_STEPS: the Maxwellian
+ *                         attractor and standard compressibility only);
  *                         TMA covers D3Q27 with FP32 / BF16 / FP16 storage, nx a multiple of 128,
- *                         the same collision, and no slab. An explicit choice the configuration
+ *                         the Maxwellian attractor, standard compressibility, and no slab. An
+ *                         explicit choice the configuration
  *                         cannot use fails with CMLBM_ERR_UNSUPPORTED.
  */
 typedef struct {
