@@ -118,8 +118,8 @@ typedef struct cmlbm cmlbm_t;
  *                         attractor and standard compressibility only);
  *                         TMA covers D3Q27 with FP32 / BF16 / FP16 storage, nx a multiple of 128,
  *                         the Maxwellian attractor, standard compressibility, and no slab. An
- *                         explicit choice the configuration
- *                         cannot use fails with CMLBM_ERR_UNSUPPORTED.
+ *                         explicit choice the configuration cannot use fails with
+ *                         CMLBM_ERR_UNSUPPORTED.
  */
 typedef struct {
     int lattice;
