@@ -5,8 +5,9 @@ The mistakes are the ones a restatement of the paper could plausibly make: a dro
 sign-flipped F/2 in the velocity, a source without its sigma/2 feedback or with the wrong
 factor, a wrong Maxwellian moment, central moments about the wrong velocity, a transposed
 stream, swapped third/fourth-order rates, a wrong eddy-viscosity
-constant, a flipped moving-wall term, an initial state without its -S/2 term, and a 3D
-factorized attractor built over the wrong axes.
+constant, a flipped moving-wall term, an initial state without its -S/2 term, a 3D factorized
+attractor built over the wrong axes, and in the turbulence closure an eddy stress without its
+factor 2, an unsymmetrised strain rate and a van Driest wall distance without the half cell.
 """
 import inspect
 import os
@@ -16,9 +17,11 @@ import torch
 
 import test_oracle_basis as TB
 import test_oracle_collision as TC
+import test_oracle_filtered as TFI
 import test_oracle_flows as TF
 import test_oracle_les as TL
 from oracle import collision as C
+from oracle import filtered as FL
 from oracle import les as L
 from oracle import moments as M
 from oracle import stream as ST
@@ -56,7 +59,7 @@ def _calls(module, include_slow=()):
 def _failures(include_slow=(), first=False):
     """Names of the pins that fail (only the first one with first=True)."""
     failed = []
-    for mod in (TB, TC, TF, TL):
+    for mod in (TB, TC, TF, TL, TFI):
         for name, thunk in _calls(mod, include_slow):
             try:
                 thunk()
@@ -119,11 +122,29 @@ MUTATIONS = {
         mp, ST, "_wall_terms",
         lambda f: lambda lat, i, shape, bc, uw, sign: (lambda m, w: (m, -w))(*f(lat, i, shape, bc, uw, sign))),
     "initial state without -S/2": lambda mp: _wrap(mp, C, "equilibrium", lambda f: lambda rho, u, F, lat: f(rho, u, 0 * F, lat)),
+    "eddy stress without its factor 2": lambda mp: _wrap(
+        mp, FL, "eddy_stress", lambda f: lambda u, cs, d: {k: 0.5 * v for k, v in f(u, cs, d).items()}),
+    "strain rate not symmetrised": lambda mp: mp.setattr(
+        FL, "strain_rate", lambda u, d: {(i, j): FL._d(u[j], i) for i in range(d) for j in range(d)}),
+    "van Driest wall distance without the half cell": lambda mp: mp.setattr(L, "van_driest_cs", _vd_full_cells),
     "factorized (2,2,0) over the wrong axes": lambda mp: _wrap(mp, C, "_factorized_attractor",
                                                               _wrong_axes((2, 2, 0), (2, 0, 0), (0, 0, 2))),
     "factorized (2,0,2) over the wrong axes": lambda mp: _wrap(mp, C, "_factorized_attractor",
                                                               _wrong_axes((2, 0, 2), (2, 0, 0), (0, 2, 0))),
 }
+
+
+def _vd_full_cells(cs, ny, nz, nx, aplus, utau_over_nu, wall_axis=1):
+    """van Driest damping with the wall distance counted in whole cells (y = j) instead of to
+    the half-way wall (y = j + 1/2)."""
+    n = (nx, ny, nz)[wall_axis]
+    j = torch.arange(n, dtype=torch.float64)
+    y = torch.minimum(j, n - 1.0 - j)
+    c = cs * (1.0 - torch.exp(-(y * utau_over_nu) / aplus))
+    shape = [1, 1, 1]
+    shape[2 - wall_axis] = n
+    full = [nz, ny, nx]
+    return c.view(*shape).expand(*full).clone()
 
 
 def _wrong_axes(target, m1, m2):
