@@ -23,6 +23,7 @@ def velocity_loss(sim_args, s0, F, target, steps, sim_kwargs=None):
 
 
 def loss_and_grad(sim_args, s0, F, target, steps, sim_kwargs=None):
+    """(L, dL/dF) by reverse-mode automatic differentiation through the oracle's steps."""
     Fp = torch.as_tensor(F, dtype=DT).detach().clone().requires_grad_(True)
     L = velocity_loss(sim_args, torch.as_tensor(s0, dtype=DT).detach(), Fp, torch.as_tensor(target, dtype=DT),
                       steps, sim_kwargs)

@@ -59,6 +59,7 @@ def discrete_shear_mode(A, k, cs, y):
     s1 = math.sin(k)
 
     def T(yy):
+        """T_xy at rows yy."""
         c = torch.cos(k * yy)
         return cs * cs * A * A * s1 * s1 * c.abs() * c
 

@@ -34,15 +34,18 @@ class Lattice:
 
     @property
     def Q(self):
+        """Number of particle velocities."""
         return self.e.shape[0]
 
 
 def _d2q9_velocities():
+    """D2Q9 particle velocities in the order of the basis columns (Sec. 2, Eq. velocityd2q9)."""
     return [(0, 0, 0), (1, 0, 0), (0, 1, 0), (-1, 0, 0), (0, -1, 0),
             (1, 1, 0), (-1, 1, 0), (-1, -1, 0), (1, -1, 0)]
 
 
 def _d3q27_velocities():
+    """D3Q27 velocities {-1, 0, 1}^3 at index 9 (e_z + 1) + 3 (e_y + 1) + (e_x + 1) (3D reading of Sec. 2)."""
     v = [None] * 27
     for ez, ey, ex in itertools.product((-1, 0, 1), repeat=3):
         v[9 * (ez + 1) + 3 * (ey + 1) + (ex + 1)] = (ex, ey, ez)
@@ -50,6 +53,7 @@ def _d3q27_velocities():
 
 
 def _weights(vel):
+    """Rest weights w_alpha of the discrete Maxwellian at rho = 1, u = 0 (Sec. 4)."""
     # Textbook rest weights: products of the 1D weights (1/6, 2/3, 1/6) per axis.
     # Pinned by the test that the equilibrium at rho=1, u=0 reproduces them.
     w1 = {-1: 1.0 / 6.0, 0: 2.0 / 3.0, 1: 1.0 / 6.0}
@@ -60,6 +64,7 @@ def _weights(vel):
 
 
 def _opposites(vel):
+    """Index of -e_alpha for every alpha (the bounce-back partner)."""
     idx = {v: i for i, v in enumerate(vel)}
     return [idx[(-a, -b, -c)] for (a, b, c) in vel]
 
@@ -70,6 +75,7 @@ D2Q9_MONOMIALS = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (2, 0, 0), (0, 2, 0),
 
 
 def _d3q27_monomials():
+    """The 27 monomials x^a y^b z^c, a, b, c in {0, 1, 2}, by increasing total order (3D reading of Sec. 2)."""
     m = list(itertools.product((0, 1, 2), repeat=3))
     m.sort(key=lambda a: (sum(a), a[::-1]))   # increasing total order
     return m
@@ -122,6 +128,7 @@ def monomial_matrix(e, monomials):
 
 
 def _build(name):
+    """Velocities, weights, opposites, monomials and the orthogonal basis K of a lattice (Sec. 2)."""
     if name == "D2Q9":
         vel = _d2q9_velocities()
         mono = D2Q9_MONOMIALS
@@ -145,6 +152,7 @@ D3Q27 = _build("D3Q27")
 
 
 def get(name):
+    """The lattice object for \"D2Q9\" or \"D3Q27\"."""
     return {"D2Q9": D2Q9, "D3Q27": D3Q27}[name]
 
 

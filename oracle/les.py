@@ -39,6 +39,7 @@ def nonequilibrium_stress(kap, rho, lat):
 
 
 def stress_norm(Pi):
+    """|Pi| = (Pi : Pi)^(1/2) of the symmetric non-equilibrium stress (reading of the Smagorinsky closure)."""
     return torch.sqrt(sum(v * v for v in Pi.values()))
 
 

@@ -93,4 +93,5 @@ def central_to_populations(kappa, u, lat):
 
 
 def zeros_like_field(shape):
+    """An FP64 zero field of the given shape."""
     return torch.zeros(shape, dtype=DT)

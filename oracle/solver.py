@@ -38,6 +38,7 @@ class OracleSim:
 
     # ---- set-up -------------------------------------------------------------------
     def set_force(self, uniform=(0.0, 0.0, 0.0), field=None):
+        """Body force F (Eqs. densitycalculation, velocitycalculation): a uniform vector plus an optional [3, ...] field."""
         self.F_uniform = torch.zeros((3,) + self.shape, dtype=DT)
         for d in range(3):
             self.F_uniform[d] += float(uniform[d])
@@ -57,13 +58,16 @@ class OracleSim:
         self.s = ST.unstream(fbar, self.lat, self.bc, self.uw)
 
     def set_state(self, s):
+        """Replace the stored post-collision populations (FP64)."""
         self.s = torch.as_tensor(s, dtype=DT).reshape((self.lat.Q,) + self.shape).clone()
 
     # ---- dynamics -----------------------------------------------------------------
     def pre_collision(self):
+        """The streamed field fbar_alpha(x) = s_alpha(x - e_alpha) (Eq. cascadedstreaming1) with the boundaries."""
         return ST.pull(self.s, self.lat, self.bc, self.uw)
 
     def step(self, n=1):
+        """n steps of stream and collide (procedure of Sec. 11)."""
         for _ in range(n):
             g = self.pre_collision()
             self.s = C.collide(g, self.F, self.lat, self.p, self.cs_eff)
@@ -77,6 +81,7 @@ class OracleSim:
         self.F = rho * FL.turbulence_acceleration(u, cs, self.lat.d) + base
 
     def step_filtered(self, n, cs):
+        """n steps of the filtered equation: closure force, then a step (Sec. 14 reading)."""
         for _ in range(n):
             self.turbulence_force(cs)
             self.step(1)

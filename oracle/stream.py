@@ -24,6 +24,7 @@ BOUNCEBACK = "bounceback"
 
 
 def _coord(n, shape_axis, ndim=3):
+    """Integer coordinates 0 .. n-1 along one axis of a [nz, ny, nx] field, broadcastable."""
     view = [1, 1, 1]
     view[shape_axis] = n
     return torch.arange(n).view(*view)
