@@ -85,6 +85,12 @@ CASES = {
                                                        wall_velocity=[[[0, 0, 0], [0, 0, 0]], [[0.02, 0, 0], [0, 0, 0]],
                                                                       [[0, 0, 0.01], [0, -0.02, 0]]])),
     "d2q9_unforced_unit_rates": dict(lattice="D2Q9", shape=(1, 20, 30), flow="tgv_unforced", kw=dict(tau=0.6)),
+    # tiny and degenerate boxes: 4^3 periodic, an odd 3 x 5 x 7 box with walls on every axis, and
+    # a channel one cell thick between its walls (both y links of every cell bounce back)
+    "tiny_periodic_4cube": dict(lattice="D3Q27", shape=(4, 4, 4), flow="tgv", kw=dict(tau=0.6)),
+    "tiny_odd_all_walls": dict(lattice="D3Q27", shape=(7, 5, 3), flow="tgv", kw=dict(tau=0.65, bc=("bounceback",) * 3)),
+    "one_cell_thick_channel": dict(lattice="D3Q27", shape=(6, 1, 8), flow="channel",
+                                   kw=dict(tau=0.7, bc=("periodic", "bounceback", "periodic"))),
 }
 
 
