@@ -73,3 +73,19 @@ def test_van_driest_profile():
     ref = 0.1 * (1 - torch.exp(-y * 10.0 / 26.0))
     assert torch.allclose(c[0, :, 0], ref, atol=0, rtol=1e-15)
     assert math.isclose(c[0, 0, 0].item(), c[0, 7, 0].item())
+
+
+def test_van_driest_damping_properties():
+    """Properties the damping must have whatever its formula: symmetric about the channel centre,
+    increasing from the wall to the centre, below the undamped constant everywhere, close to it
+    far from the walls, and vanishing as the wall distance in wall units goes to zero."""
+    ny = 16
+    c = les.van_driest_cs(0.1, ny, 1, 1, 26.0, 3.0)[0, :, 0]
+    assert torch.equal(c, c.flip(0))
+    half = c[: ny // 2]
+    assert bool((half[1:] > half[:-1]).all())
+    assert bool((c < 0.1).all())
+    far = les.van_driest_cs(0.1, ny, 1, 1, 26.0, 1e3)[0, :, 0]
+    assert bool(((0.1 - far) < 1e-6).all())
+    near = les.van_driest_cs(0.1, ny, 1, 1, 26.0, 1e-6)[0, :, 0]
+    assert bool((near < 1e-7).all())
