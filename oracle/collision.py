@@ -147,12 +147,14 @@ def _factorized_attractor(kM, post2, rho, lat):
     Second order keeps the Maxwellian attractor.
 
     The paper gives the factorized attractor for D2Q9 only. The D2Q9 form is pinned against the
-    printed element-wise kernel (``literal.py``). The 3D rules of every moment with at most two
-    non-zero exponents are pinned to it: a one-cell-thick D3Q27 run of a 2D flow in the x-y,
-    x-z or y-z plane reproduces the D2Q9 run. Parity unpinned for the moments with three
-    non-zero exponents ((1,1,1), (2,1,1) and its permutations, (2,2,1) and its permutations,
-    (2,2,2)): they are pinned only by reducing to the Maxwellian attractor when the second-order
-    moments are at equilibrium.
+    printed element-wise kernel (``literal.py``) with and without a force and at rho != 1 (the
+    printed product lacks the 1/rho, and its force terms are sigma_xxyy / 2: the residual between
+    the two forms is derived and asserted order by order). The 3D rules of every moment with at
+    most two non-zero exponents are pinned to it: a one-cell-thick D3Q27 run of a 2D flow in the
+    x-y, x-z or y-z plane reproduces the D2Q9 run. The moments with three non-zero exponents are
+    pinned by Sec. 13's postulate itself: for a state with one axis independent of the other two
+    (a product of a 1D marginal and a 2D joint at its own factorized attractor) the attractors of
+    every order are that state's own central moments, products of the marginals' moments.
     """
     idx = {a: k for k, a in enumerate(lat.monomials)}
     out = kM.clone()

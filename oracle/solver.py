@@ -16,10 +16,27 @@ from . import les as L
 from . import filtered as FL
 
 
+STORAGE_DTYPES = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}
+
+
+def round_to_storage(s, w, storage):
+    """The stored state of a library run in `storage`: each population as its deviation from the
+    rest weight, d = f / w - 1, rounded to the nearest value of the storage type (ties to even;
+    torch's conversion, a library primitive), then decoded f = w (1 + d) in float64. None or
+    "f64" leaves s unchanged. Paper silent (storage formats are not in the paper)."""
+    if storage in (None, "f64"):
+        return s
+    wv = w.view(-1, *([1] * (s.dim() - 1)))
+    d = (s / wv - 1.0).to(STORAGE_DTYPES[storage]).to(DT)
+    return wv * (1.0 + d)
+
+
 class OracleSim:
     def __init__(self, lattice, nx, ny, nz=1, params=None, bc=("periodic",) * 3,
-                 wall_velocity=None, van_driest=None):
-        """van_driest = (A_plus, u_tau / nu_0) damps C_s by the distance to the y walls."""
+                 wall_velocity=None, van_driest=None, storage=None):
+        """van_driest = (A_plus, u_tau / nu_0) damps C_s by the distance to the y walls.
+        storage = "f32" | "bf16" | "f16" rounds the stored state after initialisation and after
+        every step as a library run with that storage does (round_to_storage); None keeps FP64."""
         self.lat = get_lattice(lattice) if isinstance(lattice, str) else lattice
         if self.lat.d == 2 and nz != 1:
             raise ValueError("D2Q9 needs nz = 1")
@@ -35,6 +52,7 @@ class OracleSim:
             aplus, utau_nu = van_driest
             self.cs_eff = L.van_driest_cs(self.p.cs_smag, ny, nz, nx, aplus, utau_nu, wall_axis=1)
         self.s = torch.zeros((self.lat.Q,) + self.shape, dtype=DT)
+        self.storage = storage
 
     # ---- set-up -------------------------------------------------------------------
     def set_force(self, uniform=(0.0, 0.0, 0.0), field=None):
@@ -55,7 +73,7 @@ class OracleSim:
             # Sec. 12: the momentum is rho0 u, so the equilibrium is centred on rho0 u / rho
             u = u * (self.p.rho0 / rho)
         fbar = C.equilibrium(rho, u, self.F, self.lat)
-        self.s = ST.unstream(fbar, self.lat, self.bc, self.uw)
+        self.s = round_to_storage(ST.unstream(fbar, self.lat, self.bc, self.uw), self.lat.w, self.storage)
 
     def set_state(self, s):
         """Replace the stored post-collision populations (FP64)."""
@@ -70,7 +88,7 @@ class OracleSim:
         """n steps of stream and collide (procedure of Sec. 11)."""
         for _ in range(n):
             g = self.pre_collision()
-            self.s = C.collide(g, self.F, self.lat, self.p, self.cs_eff)
+            self.s = round_to_storage(C.collide(g, self.F, self.lat, self.p, self.cs_eff), self.lat.w, self.storage)
 
     def turbulence_force(self, cs):
         """Set F = rho a' from the Smagorinsky closure of the current resolved field (Sec. 14)."""

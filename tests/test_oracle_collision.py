@@ -261,3 +261,112 @@ def test_factorized_attractor_keeps_the_maxwellian_fixed_point(name):
     feq = C.equilibrium(rho, u, F, lat)
     post = C.collide(feq, F, lat, C.Params(tau=0.7, omega3=1.2, omega4=0.9, attractor="factorized"))
     assert (post - feq).abs().max().item() < 1e-15
+
+
+def test_factorized_literal_vs_generic_with_force_residual_structure():
+    """Eq. factorxxyyfinal as printed (Sec. 13), with F != 0 and rho != 1, against the generic
+    factorized step. The printed brackets are the post-collision second-order central moments
+    k~_xx, k~_yy (pre-collision kbar_dd plus the 6 g3 +- 2 g4 of the kernel), and the printed force
+    terms are sigma_xxyy / 2 of the hierarchy (Eq. centralmomentforcingtransformed expanded), so
+    the printed transformed attractor is k~_xx k~_yy - sigma_xxyy / 2, where the reading divides the
+    product by rho: k~_xx k~_yy / rho - sigma_xxyy / 2. It replaces rho / 9 in g8, which itself
+    subtracts sigma'_xxyy / 2 again, as for the Maxwellian attractor. Hence, printed minus generic
+    post-collision central moments: 0 at orders <= 2; omega3 sigma at third order (g6, g7 are
+    those of Sec. 10); omega4 [k~_xx k~_yy (1 - 1/rho) - sigma_xxyy / 2 - u_y sigma_xxy
+    - u_x sigma_xyy] at fourth order."""
+    lat = L.D2Q9
+    fb, F = _state(lat, 256, 25)
+    p = C.Params(tau=0.7, omega3=1.3, omega4=0.9, attractor="factorized")
+    om = (1 / 0.7, 1 / 0.7, 1 / 0.7, 1.3, 1.3, 0.9)
+    post_l, _, _ = LIT.collide_literal(fb, F, om, factorized=True)
+    post_g = C.collide(fb, F, lat, p)
+    rho, u = C.hydrodynamics(fb, F, lat)
+    assert (rho - 1).abs().min().item() > 1e-4 and F.abs().max().item() > 1e-3
+    kl = M.central_moments(post_l, u, lat)
+    kg = M.central_moments(post_g, u, lat)
+    sig, _ = C.source_central(M.central_moments(fb, u, lat), rho, F, lat)
+    for j in range(6):
+        assert (kl[j] - kg[j]).abs().max().item() < 2e-15, j
+    assert torch.allclose(kl[6] - kg[6], 1.3 * sig[6], atol=1e-16, rtol=1e-10)
+    assert torch.allclose(kl[7] - kg[7], 1.3 * sig[7], atol=1e-16, rtol=1e-10)
+    ref8 = 0.9 * (kg[3] * kg[4] * (1 - 1 / rho) - 0.5 * sig[8] - u[1] * sig[6] - u[0] * sig[7])
+    assert ref8.abs().max().item() > 1e-3
+    assert torch.allclose(kl[8] - kg[8], ref8, atol=1e-15, rtol=1e-10)
+
+
+def _one_axis(g, n, u, theta):
+    """Populations on e = -1, 0, 1 with mean u and central second moment theta:
+    p(+-1) = (theta + u^2 +- u) / 2, p(0) = 1 - theta - u^2."""
+    q = theta + u * u
+    return torch.stack([(q - u) / 2, 1 - q, (q + u) / 2])
+
+
+def _partially_factorized_state(split, n, seed):
+    """rho p_a(e_a) q_bc(e_b, e_c): axis a independent of the pair (b, c), with a random 1D
+    marginal p_a and a random positive 9-point joint q_bc (correlated b and c)."""
+    g = torch.Generator().manual_seed(seed)
+    lat = L.D3Q27
+    rho = 0.8 + 0.5 * torch.rand(n, generator=g, dtype=DT)
+    ua = 0.1 * torch.randn(n, generator=g, dtype=DT)
+    ta = 0.28 + 0.1 * torch.rand(n, generator=g, dtype=DT)
+    pa = _one_axis(g, n, ua, ta)                                         # [3, n] over e_a
+    q = 0.5 + torch.rand(3, 3, n, generator=g, dtype=DT)                 # [e_b, e_c, n]
+    q = q / q.sum((0, 1))
+    b, c = [d for d in range(3) if d != split]
+    f = torch.empty(27, n, dtype=DT)
+    for i in range(27):
+        e = [int(v) for v in lat.e[i]]
+        f[i] = rho * pa[e[split] + 1] * q[e[b] + 1, e[c] + 1]
+    return f, rho
+
+
+@pytest.mark.parametrize("split", [0, 1, 2])
+def test_factorized_3d_attractors_of_partially_factorized_states(split):
+    """Sec. 13's postulate: the attractors are products of post-collision lower-order central
+    moments, as for a distribution that factorizes over its Cartesian components. For a state
+    whose axis a is independent of the pair (b, c), its central moments are products
+    kappa_(a-part, bc-part) = rho m_a * M_bc of the marginals' moments (m_0 = 1, m_1 = 0,
+    m_2 = theta_a; M_00 = 1, M_10 = M_01 = 0, M_20 = theta_b, M_02 = theta_c, M_11 = c_bc, and,
+    with the pair at its own (D2Q9) factorized attractor, M_21 = M_12 = 0, M_22 = theta_b theta_c).
+    With omega3 = omega4 = 1 and F = 0 a step leaves every moment of order >= 3 at its attractor,
+    so those of the output must be these products of the output's own second-order moments
+    (theta = kappa~_dd / rho, c_bc = kappa~_bc / rho). Every one of the eight moments with three
+    non-zero exponents enters: (2,1,1) with the 2 on axis a is rho theta_a c_bc, (2,2,2) is
+    rho theta_x theta_y theta_z, the others vanish."""
+    lat = L.D3Q27
+    fb, rho = _partially_factorized_state(split, 64, 30 + split)
+    F = torch.zeros(3, fb.shape[1], dtype=DT)
+    p = C.Params(tau=0.7, omega_bulk=1.3, omega3=1.0, omega4=1.0, attractor="factorized")
+    post = C.collide(fb, F, lat, p)
+    _, u = C.hydrodynamics(fb, F, lat)
+    K = M.central_moments(post, u, lat)
+    idx = {a: k for k, a in enumerate(lat.monomials)}
+    b, c = [d for d in range(3) if d != split]
+
+    def mono(exps):
+        return idx[tuple(exps)]
+
+    theta = []
+    for d in range(3):
+        e = [0, 0, 0]
+        e[d] = 2
+        theta.append(K[mono(e)] / rho)
+    e = [0, 0, 0]
+    e[b] = e[c] = 1
+    cbc = K[mono(e)] / rho
+    assert cbc.abs().max().item() > 1e-2                 # the pair really is correlated
+    m = {0: torch.ones_like(rho), 1: torch.zeros_like(rho), 2: theta[split]}
+    Mbc = {(0, 0): torch.ones_like(rho), (1, 0): 0 * rho, (0, 1): 0 * rho, (2, 0): theta[b], (0, 2): theta[c],
+           (1, 1): cbc, (2, 1): 0 * rho, (1, 2): 0 * rho, (2, 2): theta[b] * theta[c]}
+    nonzero_three = 0
+    for a in lat.monomials:
+        if sum(a) < 3:
+            continue
+        want = rho * m[a[split]] * Mbc[(a[b], a[c])]
+        assert torch.allclose(K[idx[a]], want, atol=1e-15, rtol=1e-12), a
+        if min(a) > 0 and want.abs().max().item() > 1e-6:
+            nonzero_three += 1
+    assert nonzero_three == 2            # (2,1,1) on axis a and (2,2,2)
+    # the Maxwellian attractor gives different higher moments for the same state
+    post_m = C.collide(fb, F, lat, C.Params(tau=0.7, omega_bulk=1.3))
+    assert (M.central_moments(post_m, u, lat) - K).abs().max().item() > 1e-4

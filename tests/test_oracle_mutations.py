@@ -5,8 +5,9 @@ The mistakes are the ones a restatement of the paper could plausibly make: a dro
 sign-flipped F/2 in the velocity, a source without its sigma/2 feedback or with the wrong
 factor, a wrong Maxwellian moment, central moments about the wrong velocity, a transposed
 stream, swapped third/fourth-order rates, a wrong eddy-viscosity
-constant, a flipped moving-wall term, an initial state without its -S/2 term, a 3D factorized
-attractor built over the wrong axes, and in the turbulence closure an eddy stress without its
+constant, a flipped moving-wall term, an initial state without its -S/2 term, 3D factorized
+attractors built over the wrong axes, divided by one power of rho too many, from the
+pre-collision second-order moments, or non-zero where a factor vanishes, and in the turbulence closure an eddy stress without its
 factor 2, an unsymmetrised strain rate and a van Driest wall distance without the half cell.
 """
 import inspect
@@ -131,7 +132,52 @@ MUTATIONS = {
                                                               _wrong_axes((2, 2, 0), (2, 0, 0), (0, 0, 2))),
     "factorized (2,0,2) over the wrong axes": lambda mp: _wrap(mp, C, "_factorized_attractor",
                                                               _wrong_axes((2, 0, 2), (2, 0, 0), (0, 2, 0))),
+    "factorized products over rho^k instead of rho^(k-1)": lambda mp: _wrap(mp, C, "_factorized_attractor",
+                                                                           _extra_rho),
+    "factorized from the pre-collision second-order moments": lambda mp: _pre_collision_factors(mp),
+    "factorized (2,1,1) with the wrong off-diagonal": lambda mp: _wrap(mp, C, "_factorized_attractor",
+                                                                      _wrong_axes((2, 1, 1), (2, 0, 0), (1, 1, 0))),
+    "factorized (1,2,1) with the wrong diagonal": lambda mp: _wrap(mp, C, "_factorized_attractor",
+                                                                  _wrong_axes((1, 2, 1), (2, 0, 0), (1, 0, 1))),
+    "factorized (2,2,1) not zero": lambda mp: _wrap(mp, C, "_factorized_attractor",
+                                                    _wrong_axes((2, 2, 1), (2, 0, 0), (0, 1, 1))),
 }
+
+
+def _extra_rho(f):
+    """Every factorized product of order >= 3 divided by rho once more."""
+    def g(kM, post2, rho, lat):
+        out = f(kM, post2, rho, lat)
+        for k, a in enumerate(lat.monomials):
+            if sum(a) >= 3:
+                out[k] = out[k] / rho
+        return out
+    return g
+
+
+def _pre_collision_factors(mp):
+    """The factorized attractor built from the pre-collision second-order central moments (the
+    collision's own central-moment transform is recorded and its values used in place of the
+    relaxed ones)."""
+    seen = {}
+    orig_cm = M.central_moments
+
+    def central_moments(f, u, lat):
+        out = orig_cm(f, u, lat)
+        seen["k"] = out
+        return out
+
+    orig_fa = C._factorized_attractor
+
+    def factorized(kM, post2, rho, lat):
+        pre = post2.clone()
+        for k, a in enumerate(lat.monomials):
+            if sum(a) == 2:
+                pre[k] = seen["k"][k]
+        return orig_fa(kM, pre, rho, lat)
+
+    mp.setattr(M, "central_moments", central_moments)
+    mp.setattr(C, "_factorized_attractor", factorized)
 
 
 def _vd_full_cells(cs, ny, nz, nx, aplus, utau_over_nu, wall_axis=1):
