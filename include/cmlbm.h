@@ -200,10 +200,20 @@ CMLBM_API int cmlbm_moments(cmlbm_t* h, double* rho, double* u, int where);
 /* Same as cmlbm_moments for an arbitrary state buffer (device, handle layout). */
 CMLBM_API int cmlbm_moments_of(cmlbm_t* h, const void* state, double* rho, double* u);
 
-/* FP64 reductions of the current field: out = {sum rho, sum rho u_x, sum rho u_y,
- * sum rho u_z, sum rho |u|^2 / 2} (host array, synchronous, deterministic order).
- * Returns CMLBM_ERR_DIVERGED if any of them is not finite, and CMLBM_ERR_CUDA if a TMA-staged
- * step since the last check gave up on a bounded pipeline wait (its output is then invalid). */
+/* FP64 reductions of the current field: out = {sum rho, sum j_x, sum j_y, sum j_z,
+ * sum rho |u|^2 / 2} (host array, synchronous, deterministic order), where j = sum fbar e + F/2
+ * is the momentum of Eq. velocitycalculation (rho u; rho0 u in the reduced-compressibility form of
+ * Sec. 12, whose velocity is u = j / rho0). Each cell's values are computed in the arithmetic
+ * precision and summed in FP64. Returns CMLBM_ERR_DIVERGED if any of the five is not finite (a
+ * NaN or infinity anywhere in the field reaches the sums), and CMLBM_ERR_CUDA if a TMA-staged step
+ * since the last check gave up on a bounded pipeline wait (its output is then invalid).
+ *
+ * TMA-staged steps report a pipeline wait that gave up through a device flag. Its value is copied
+ * to the host after every cmlbm_step / cmlbm_step_buffers call, asynchronously; every call that
+ * returns results (cmlbm_step, cmlbm_step_buffers, cmlbm_moments, cmlbm_moments_of,
+ * cmlbm_get_state, cmlbm_reduce) checks it on entry, and the synchronising ones (cmlbm_reduce and
+ * the CMLBM_HOST forms of cmlbm_moments and cmlbm_get_state) check it again once the stream is
+ * drained. A failure is reported once, by CMLBM_ERR_CUDA, and the flag is then cleared. */
 CMLBM_API int cmlbm_reduce(cmlbm_t* h, double out[5]);
 
 /* Bytes of one state buffer: Q * N * storage size, or Q * nx * ny * (nz + 2) * storage size
@@ -245,6 +255,17 @@ CMLBM_API int cmlbm_adjoint_terminal(cmlbm_t* h, const void* state, const double
  * lambda_out = dL/ds_t (must not alias lambda_in); adds (dC/dF)^T lambda_in into dLdF. */
 CMLBM_API int cmlbm_step_adjoint(cmlbm_t* h, const void* state, const void* lambda_in, void* lambda_out, double* dLdF);
 
+/* cmlbm_step_adjoint with the force gradient of the step, (dC/dF)^T lambda_in, added into a
+ * segment accumulator seg ([3][N] device array in the arithmetic precision: FP32 for F32
+ * storage, FP64 for F64) instead of into dLdF. With fold != 0, seg with this step's term is then
+ * added into the FP64 dLdF and seg is set to zero. A reverse sweep over a checkpoint segment
+ * passes fold = 1 on its last call (the segment's first step): the per-step traffic of the
+ * accumulator is then 2 x 12 bytes per cell at FP32 instead of 2 x 24, and the sum over
+ * segments stays in FP64. seg must be zero before the first call of a segment (cudaMemset, or
+ * a previous fold). Errors as for cmlbm_step_adjoint, and CMLBM_ERR_INVALID for a NULL seg. */
+CMLBM_API int cmlbm_step_adjoint_segment(cmlbm_t* h, const void* state, const void* lambda_in, void* lambda_out,
+                                         void* seg, double* dLdF, int fold);
+
 /* ---- slab decomposition along z (no counterpart in the paper) -------------------------- *
  * A periodic-in-z D3Q27 domain split into z-slabs, one handle per slab, each created with
  * bc[2] = CMLBM_HALO and nz = its own number of planes. The streaming step (Eq.
@@ -262,6 +283,21 @@ CMLBM_API int cmlbm_step_adjoint(cmlbm_t* h, const void* state, const void* lamb
  * single domain; the TMA step, the adjoint and turbulence forcing return
  * CMLBM_ERR_UNSUPPORTED on a slab handle. */
 enum { CMLBM_FACE_BOTTOM = 0, CMLBM_FACE_TOP = 1 };
+
+/* One step like cmlbm_step(h, 1), split so that a slab's face exchange can overlap its update:
+ * the first and last planes (z = 0 and nz - 1, the only ones whose pull reads the ghost planes,
+ * and the only ones the next face messages come from) are launched on the handle's stream, the
+ * interior planes 1 .. nz - 2 on a stream of the library's own. A pack issued on the handle's
+ * stream right after this call waits only for the two boundary planes, and the unpacks write
+ * ghost planes that the interior launch does not read, so the exchange proceeds while the
+ * interior runs. The next split step orders its boundary planes after this interior (they pull
+ * from planes 1 and nz - 2) and its interior after everything issued on the handle's stream
+ * before it; every other call that reads or writes the state or the force (cmlbm_step,
+ * cmlbm_moments, cmlbm_reduce, cmlbm_get_state, ...) first orders the handle's stream after the
+ * interior. Same results, bit for bit, as cmlbm_step(h, 1). Any handle with the direct or
+ * two-cells-per-thread kernel (CMLBM_ERR_UNSUPPORTED for the TMA-staged and two-steps kernels);
+ * meant for slabs. The private stream and two events are created on the first call. */
+CMLBM_API int cmlbm_step_split(cmlbm_t* h);
 
 /* Bytes of one face message: 9 * nx * ny values in the storage format. */
 CMLBM_API size_t cmlbm_halo_bytes(const cmlbm_t* h);
@@ -289,14 +325,16 @@ CMLBM_API long long cmlbm_launch_count(const cmlbm_t* h);
 CMLBM_API int cmlbm_step_kernel(const cmlbm_t* h);
 
 /* ---- allocation-free reduction (no counterpart in the paper) --------------------------- *
- * The FP64 reductions of cmlbm_reduce for callers that cannot allocate device memory: code
- * recorded into a CUDA graph under capture, hosts whose device memory is owned by another
- * allocator, or tools that must not create a handle (cmlbm_create allocates two state buffers).
+ * The FP64 reductions of cmlbm_reduce for callers that cannot allocate device memory: a host
+ * whose device memory is all handed out up front to another allocator (a framework's memory
+ * pool, where an outside cudaMalloc fails or fragments the pool), a loop with a fixed memory
+ * budget that must not grow its footprint while it runs, or a tool that must not create a
+ * handle (cmlbm_create allocates two state buffers).
  * No handle and no allocation: the caller passes the configuration, a state buffer in the
  * library's layout and storage format (device, Q*N elements), the force (uniform[3] added
  * everywhere, NULL = 0; force_field = device [3][N] array in the arithmetic type -- double for
  * CMLBM_F64 storage, float otherwise -- or NULL), and out, a device array of 5 doubles that
- * receives {sum rho, sum rho u_x, sum rho u_y, sum rho u_z, sum rho |u|^2 / 2}.
+ * receives {sum rho, sum j_x, sum j_y, sum j_z, sum rho |u|^2 / 2} as cmlbm_reduce defines them.
  * Launches asynchronously on cfg->stream (device cfg->device); the caller synchronises.
  * Scratch: the per-block partial sums live in one file-scope device array of 16384 x 5
  * doubles (640 KiB on every GPU that loads the library, kept until the process exits), so
@@ -305,7 +343,10 @@ CMLBM_API int cmlbm_step_kernel(const cmlbm_t* h);
  * clearing between calls, but all calls share the array: calls that overlap on the GPU
  * (different streams, or host threads racing) corrupt each other's sums. The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress, with that device
- * current); make that first call before any stream capture begins.
+ * current) and keeps it for the life of the process; make that first call before any stream
+ * capture begins. A cudaDeviceReset of that device unloads the library's device code and may move
+ * the array, so the kept address is no longer valid: do not call this entry point on a device
+ * after resetting it.
  * Errors: CMLBM_ERR_INVALID (NULL arguments, bad configuration, grid over the limit),
  * CMLBM_ERR_CUDA (symbol lookup or launch failure). */
 CMLBM_API int cmlbm_reduce_noalloc(const cmlbm_config* cfg, const void* state, const double uniform_force[3],

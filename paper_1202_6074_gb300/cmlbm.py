@@ -31,7 +31,7 @@ SYMBOLS = ["cmlbm_config_default", "cmlbm_create", "cmlbm_destroy", "cmlbm_last_
            "cmlbm_moments_of", "cmlbm_reduce", "cmlbm_state_bytes", "cmlbm_get_state", "cmlbm_set_state",
            "cmlbm_adjoint_terminal", "cmlbm_step_adjoint", "cmlbm_launch_count", "cmlbm_reduce_noalloc",
            "cmlbm_turbulence_force", "cmlbm_step_filtered", "cmlbm_halo_bytes", "cmlbm_halo_pack",
-           "cmlbm_halo_unpack", "cmlbm_step_kernel"]
+           "cmlbm_halo_unpack", "cmlbm_step_kernel", "cmlbm_step_adjoint_segment", "cmlbm_step_split"]
 KERNELS = {0: "auto", 1: "direct", 2: "tma", 3: "pair", 4: "pair_two_steps"}
 
 
@@ -85,6 +85,7 @@ def load():
         "cmlbm_set_force": (I, [P, D, P, I]),
         "cmlbm_init": (I, [P, P, P, I]),
         "cmlbm_step": (I, [P, I]),
+        "cmlbm_step_split": (I, [P]),
         "cmlbm_step_buffers": (I, [P, P, P]),
         "cmlbm_moments": (I, [P, P, P, I]),
         "cmlbm_moments_of": (I, [P, P, P, P]),
@@ -94,6 +95,7 @@ def load():
         "cmlbm_set_state": (I, [P, P, ctypes.c_size_t, I]),
         "cmlbm_adjoint_terminal": (I, [P, P, P, P, P, P]),
         "cmlbm_step_adjoint": (I, [P, P, P, P, P]),
+        "cmlbm_step_adjoint_segment": (I, [P, P, P, P, P, P, I]),
         "cmlbm_launch_count": (ctypes.c_longlong, [P]),
         "cmlbm_reduce_noalloc": (I, [ctypes.POINTER(Config), P, D, P, P]),
         "cmlbm_turbulence_force": (I, [P, ctypes.c_double]),
@@ -252,6 +254,11 @@ class Solver:
     def step(self, n=1):
         self._check(self.lib.cmlbm_step(self.h, int(n)))
 
+    def step_split(self):
+        """One step with the boundary planes on the handle's stream and the interior on the
+        library's own (cmlbm_step_split): a face exchange issued next overlaps the interior."""
+        self._check(self.lib.cmlbm_step_split(self.h))
+
     def turbulence_force(self, cs):
         """Set the force field to rho a' from the Smagorinsky closure (filtered equation)."""
         self._check(self.lib.cmlbm_turbulence_force(self.h, float(cs)))
@@ -337,6 +344,12 @@ class Solver:
 
     def step_adjoint(self, state, lam_in, lam_out, dLdF):
         self._check(self.lib.cmlbm_step_adjoint(self.h, _ptr(state), _ptr(lam_in), _ptr(lam_out), _ptr(dLdF)))
+
+    def step_adjoint_segment(self, state, lam_in, lam_out, seg, dLdF, fold):
+        """One step back with the force gradient added into the segment accumulator seg (arithmetic
+        type, [3, nz, ny, nx]); with fold, seg is then added into the FP64 dLdF and zeroed."""
+        self._check(self.lib.cmlbm_step_adjoint_segment(self.h, _ptr(state), _ptr(lam_in), _ptr(lam_out), _ptr(seg),
+                                                        _ptr(dLdF), 1 if fold else 0))
 
 
 def reduce_noalloc(cfg, state, out, uniform_force=(0.0, 0.0, 0.0), force_field=None):

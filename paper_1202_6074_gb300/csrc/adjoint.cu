@@ -155,12 +155,23 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_terminal(const S* __restrict
 #endif
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
+// How a step's force gradient (dC/dF)^T lambda_{t+1} is accumulated:
+//   kAccF64   into the FP64 accumulator dLdF ([3][N] doubles, read and written every step)
+//   kAccSeg   into a segment accumulator `seg` in the arithmetic type ([3][N]), which holds the
+//             sum over the steps of one checkpoint segment
+//   kAccFold  as kAccSeg, then seg (this step's term included) is added into the FP64 dLdF and
+//             seg is reset to zero: the last step of a segment in the reverse sweep
+// The segment form moves 2 x 12 bytes per cell and step instead of 2 x 24 at FP32 and keeps
+// the FP64 accumulation across segments.
+enum { kAccF64 = 0, kAccSeg = 1, kAccFold = 2 };
+
 // UNIT: omega_3 = omega_4 = 1 (the default rates), so that the post-collision moments of order
 // >= 3 are kappa^M + sigma / 2 and their adjoints need neither rate (fewer live registers)
-template <int D, class S, bool WALLS, bool UNIT = false>
+template <int D, class S, bool WALLS, bool UNIT = false, int ACC = kAccF64>
 __global__ void __launch_bounds__(kBlock, CM_ADJ_MIN_BLOCKS) k_adjoint_step(const S* __restrict__ state, const typename Codec<S>::R* __restrict__ Ff,
                                                         PR<typename Codec<S>::R> p, const typename Codec<S>::R* __restrict__ lam_in,
-                                                        typename Codec<S>::R* __restrict__ lam_out, double* __restrict__ dLdF) {
+                                                        typename Codec<S>::R* __restrict__ lam_out, double* __restrict__ dLdF,
+                                                        typename Codec<S>::R* __restrict__ seg) {
     using R = typename Codec<S>::R;
     constexpr int Q = Lat<D>::Q;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -171,13 +182,17 @@ __global__ void __launch_bounds__(kBlock, CM_ADJ_MIN_BLOCKS) k_adjoint_step(cons
     const size_t NN = p.N;
     const R* __restrict__ lam_c = lam_in + cell;      // lambda_{t+1} of this cell: lam_c[i N]
     double* __restrict__ dF_c = dLdF + cell;
+    R* __restrict__ seg_c = seg + cell;
     if (CM_ADJ_PREFETCH) {
         // lambda_{t+1} and the dL/dF accumulator are needed only after the forward
         // recomputation: start bringing them into L2 now so that their loads do not stall
 #pragma unroll
         for (int i = 0; i < Q; ++i) prefetch_l2(lam_c + NN * i);
 #pragma unroll
-        for (int d = 0; d < D; ++d) prefetch_l2(dF_c + NN * d);
+        for (int d = 0; d < D; ++d) {
+            if constexpr (ACC == kAccF64) prefetch_l2(dF_c + NN * d);
+            else prefetch_l2(seg_c + NN * d);
+        }
     }
 
     // ---- forward recomputation (plain central moments of fbar) ----
@@ -384,7 +399,16 @@ __global__ void __launch_bounds__(kBlock, CM_ADJ_MIN_BLOCKS) k_adjoint_step(cons
         lam_out[(unsigned)dir * p.N + sc] = L[slot<D>(i)];
     }
 #pragma unroll
-    for (int d = 0; d < D; ++d) dF_c[NN * d] += (double)Fb[d];
+    for (int d = 0; d < D; ++d) {
+        if constexpr (ACC == kAccF64) {
+            dF_c[NN * d] += (double)Fb[d];
+        } else if constexpr (ACC == kAccSeg) {
+            seg_c[NN * d] += Fb[d];
+        } else {
+            dF_c[NN * d] += (double)(seg_c[NN * d] + Fb[d]);
+            seg_c[NN * d] = R(0);
+        }
+    }
 }
 
 }  // namespace
@@ -402,17 +426,22 @@ cudaError_t launch_adjoint_terminal(const void* state, const void* Ff, const Par
 
 template <int D, class R>
 cudaError_t launch_adjoint_step(const void* state, const void* Ff, const Params& p, const void* lam_in, void* lam_out,
-                                double* dLdF, cudaStream_t st) {
+                                double* dLdF, void* seg, int acc, cudaStream_t st) {
     const dim3 b = cell_block(p.nx), g = cell_grid(p, b);
     const bool unit = p.omega3 == 1.0 && p.omega4 == 1.0;
-    auto go = [&](auto walls, auto u) {
-        k_adjoint_step<D, R, decltype(walls)::value, decltype(u)::value><<<g, b, 0, st>>>(
-            (const R*)state, (const R*)Ff, typed<R>(p), (const R*)lam_in, (R*)lam_out, dLdF);
+    auto go = [&](auto walls, auto u, auto a) {
+        k_adjoint_step<D, R, decltype(walls)::value, decltype(u)::value, decltype(a)::value><<<g, b, 0, st>>>(
+            (const R*)state, (const R*)Ff, typed<R>(p), (const R*)lam_in, (R*)lam_out, dLdF, (R*)seg);
+    };
+    auto by_acc = [&](auto walls, auto u) {
+        if (acc == kAccSeg) go(walls, u, std::integral_constant<int, kAccSeg>{});
+        else if (acc == kAccFold) go(walls, u, std::integral_constant<int, kAccFold>{});
+        else go(walls, u, std::integral_constant<int, kAccF64>{});
     };
     using T_ = std::true_type;
     using F_ = std::false_type;
-    if (has_walls(p)) unit ? go(T_{}, T_{}) : go(T_{}, F_{});
-    else unit ? go(F_{}, T_{}) : go(F_{}, F_{});
+    if (has_walls(p)) unit ? by_acc(T_{}, T_{}) : by_acc(T_{}, F_{});
+    else unit ? by_acc(F_{}, T_{}) : by_acc(F_{}, F_{});
     return cudaGetLastError();
 }
 
@@ -420,7 +449,7 @@ cudaError_t launch_adjoint_step(const void* state, const void* Ff, const Params&
     template cudaError_t launch_adjoint_terminal<D, R>(const void*, const void*, const Params&, const double*,     \
                                                        const double*, void*, double*, cudaStream_t);               \
     template cudaError_t launch_adjoint_step<D, R>(const void*, const void*, const Params&, const void*, void*,     \
-                                                   double*, cudaStream_t);
+                                                   double*, void*, int, cudaStream_t);
 CM_ADJ(3, double)
 CM_ADJ(3, float)
 CM_ADJ(2, double)

@@ -50,6 +50,10 @@ struct cmlbm {
     bool tma = false;
     alignas(128) unsigned char maps[2][2][128];
     int* flag = nullptr;       // device error flag of the bounded pipeline waits
+    // page-locked mirror of `flag` on TMA handles: refreshed by an asynchronous 4-byte copy after
+    // every batch of TMA-staged steps, read by the host at the start of each call that returns
+    // results and after each synchronising call, so that no call blocks just to check it
+    volatile int* hflag = nullptr;
     int nsm = 0;
     void* turb = nullptr;      // [10][N] arithmetic type: rho, u, eddy stress (turbulence forcing)
     size_t ghost = 0;          // elements before the first own plane of a state buffer (nx ny on a slab)
@@ -67,6 +71,11 @@ struct cmlbm {
 #else
     bool graphs = true;        // false after a capture failed: plain launches from then on
 #endif
+    // split steps (cmlbm_step_split): the interior planes run on a private stream; ev_begin marks
+    // the work issued on `st` before a split step, ev_interior the end of its interior launch
+    cudaStream_t inner = nullptr;
+    cudaEvent_t ev_begin = nullptr, ev_interior = nullptr;
+    bool interior_pending = false;
 };
 
 namespace {
@@ -82,6 +91,32 @@ int fail(cmlbm* h, int code, const std::string& msg) {
 int cuda_fail(cmlbm* h, cudaError_t e, const char* what) {
     std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
     return fail(h, CMLBM_ERR_CUDA, m);
+}
+
+// Test hook: with CMLBM_TEST_PIPELINE_FAULT set, every batch of TMA-staged steps is followed by
+// a write of 1 into the handle's pipeline flag, the value a step kernel stores when a bounded
+// wait runs out, so that the reporting below is tested without making any kernel wait in vain.
+bool test_pipeline_fault() { return std::getenv("CMLBM_TEST_PIPELINE_FAULT") != nullptr; }
+
+// Enqueue the refresh of the host mirror of the pipeline flag after TMA-staged steps.
+cudaError_t mirror_flag(cmlbm* h) {
+    if (!h->tma) return cudaSuccess;
+    if (test_pipeline_fault()) {
+        cudaError_t e = cudaMemsetAsync(h->flag, 1, 1, h->st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaMemcpyAsync((void*)h->hflag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->st);
+}
+
+// CMLBM_ERR_CUDA if a TMA-staged step that has completed gave up on a bounded pipeline wait (its
+// output, and everything computed from it since, is invalid). The flag is then cleared: the
+// stream is drained so that no mirror copy still in flight sets it again.
+int check_flag(cmlbm* h) {
+    if (!h->tma || !h->hflag || *h->hflag == 0) return CMLBM_OK;
+    cudaStreamSynchronize(h->st);
+    cudaMemset(h->flag, 0, sizeof(int));
+    *h->hflag = 0;
+    return fail(h, CMLBM_ERR_CUDA, "a TMA-staged step gave up on a bounded pipeline wait");
 }
 
 // Switches to the handle's device for the duration of a call and restores the caller's.
@@ -155,6 +190,27 @@ cudaError_t do_step(cmlbm* h, const void* src, void* dst) {
         using S = std::remove_pointer_t<decltype(s)>;
         return cm::launch_step<decltype(d)::value, S>(own(h, src), own(h, dst), h->force, h->p, h->st);
     });
+}
+
+// One step of the planes z0 .. z0 + nzc - 1 only (the pull still reads the whole source buffer),
+// launched on stream `on`.
+cudaError_t do_step_planes(cmlbm* h, const void* src, void* dst, int z0, int nzc, cudaStream_t on) {
+    ++h->launches;
+    cm::Params q = h->p;
+    q.z0 = z0;
+    q.nzc = nzc;
+    return dispatch(h, [&](auto d, auto* s) {
+        using S = std::remove_pointer_t<decltype(s)>;
+        return cm::launch_step<decltype(d)::value, S>(own(h, src), own(h, dst), h->force, q, on);
+    });
+}
+
+// Order the handle's stream after the interior launch of the last split step, so that whatever
+// is issued on it next sees the whole new state.
+cudaError_t join_interior(cmlbm* h) {
+    if (!h->interior_pending) return cudaSuccess;
+    h->interior_pending = false;
+    return cudaStreamWaitEvent(h->st, h->ev_interior, 0);
 }
 
 void drop_graphs(cmlbm* h) {
@@ -256,8 +312,10 @@ int cmlbm_create(const cmlbm_config* cfg, cmlbm_t** out) {
     if (c.lattice == CMLBM_D2Q9 && c.nz != 1) return fail(nullptr, CMLBM_ERR_INVALID, "D2Q9 needs nz == 1");
     const long long N = (long long)c.nx * c.ny * c.nz;
     if (N >= (1LL << 31)) return fail(nullptr, CMLBM_ERR_INVALID, "nx*ny*nz must be < 2^31");
-    if (N * (c.lattice == CMLBM_D3Q27 ? 27 : 9) >= (1LL << 32))
-        return fail(nullptr, CMLBM_ERR_INVALID, "Q*nx*ny*nz must be < 2^32 (32-bit element offsets)");
+    // D3Q27 grids with Q*N >= 2^32 elements run kernel variants with 64-bit element offsets
+    const bool big = N * (c.lattice == CMLBM_D3Q27 ? 27 : 9) >= (1LL << 32);
+    if (big && c.lattice != CMLBM_D3Q27)
+        return fail(nullptr, CMLBM_ERR_INVALID, "D2Q9 grids need 9*nx*ny < 2^32 (32-bit element offsets)");
     if (c.nz > 65535) return fail(nullptr, CMLBM_ERR_INVALID, "nz must be <= 65535");
     if (c.ny > 65535) return fail(nullptr, CMLBM_ERR_INVALID, "ny must be <= 65535");
     for (int a = 0; a < 3; ++a)
@@ -269,8 +327,19 @@ int cmlbm_create(const cmlbm_config* cfg, cmlbm_t** out) {
     const bool slab = c.bc[2] == CMLBM_HALO;
     if (slab && c.lattice != CMLBM_D3Q27) return fail(nullptr, CMLBM_ERR_INVALID, "CMLBM_HALO needs D3Q27");
     const long long S = slab ? (long long)c.nx * c.ny * (c.nz + 2) : N;
-    if (S * (c.lattice == CMLBM_D3Q27 ? 27 : 9) >= (1LL << 32))
+    if (slab && S * (c.lattice == CMLBM_D3Q27 ? 27 : 9) >= (1LL << 32))
         return fail(nullptr, CMLBM_ERR_INVALID, "Q*nx*ny*(nz+2) must be < 2^32 on a slab (32-bit element offsets)");
+    if (big) {
+        const bool pair_ok = c.storage != CMLBM_F64 && c.bc[0] == CMLBM_PERIODIC && c.nx % 64 == 0;
+        if (c.storage != CMLBM_F64 && !pair_ok)
+            return fail(nullptr, CMLBM_ERR_UNSUPPORTED,
+                        "grids with 27*N >= 2^32 need FP64 storage, or periodic x and nx a multiple of 64 "
+                        "(the two-cells-per-thread kernel)");
+        if (c.kernel == CMLBM_KERNEL_TMA || c.kernel == CMLBM_KERNEL_PAIR_TWO_STEPS ||
+            (c.kernel == CMLBM_KERNEL_DIRECT && c.storage != CMLBM_F64))
+            return fail(nullptr, CMLBM_ERR_UNSUPPORTED,
+                        "grids with 27*N >= 2^32 run the automatic kernel choice only (64-bit offsets)");
+    }
     if (slab && c.kernel == CMLBM_KERNEL_TMA)
         return fail(nullptr, CMLBM_ERR_UNSUPPORTED, "the TMA-staged step does not cover slab handles");
     if (!(c.tau > 0.5) || !std::isfinite(c.tau)) return fail(nullptr, CMLBM_ERR_INVALID, "tau must be > 1/2");
@@ -302,6 +371,7 @@ int cmlbm_create(const cmlbm_config* cfg, cmlbm_t** out) {
     p.nz = c.nz;
     p.N = N;
     p.S = S;
+    p.big = big ? 1 : 0;
     h->ghost = slab ? (size_t)c.nx * c.ny : 0;
     for (int a = 0; a < 3; ++a) p.bc[a] = c.bc[a];
     std::memcpy(p.uw, c.wall_velocity, sizeof(p.uw));
@@ -339,7 +409,7 @@ int cmlbm_create(const cmlbm_config* cfg, cmlbm_t** out) {
         return fail(nullptr, CMLBM_ERR_NOMEM, "cudaMalloc of the reduction buffers failed");
     }
     if (cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess) h->nsm = 1;
-    if (c.kernel == CMLBM_KERNEL_AUTO && cm::pair_eligible(p, h->D, c.storage != CMLBM_F64)) p.pair = 1;
+    if ((c.kernel == CMLBM_KERNEL_AUTO || big) && cm::pair_eligible(p, h->D, c.storage != CMLBM_F64)) p.pair = 1;
     const bool two_ok = cm::two_steps_eligible(p, h->D, c.storage == CMLBM_F32, slab);
     if (c.kernel == CMLBM_KERNEL_PAIR_TWO_STEPS && !two_ok) {
         cmlbm_destroy(h);
@@ -367,6 +437,16 @@ int cmlbm_create(const cmlbm_config* cfg, cmlbm_t** out) {
         bool ok = eligible;
         for (int k = 0; k < 2 && ok; ++k) ok = cm::encode_tma_maps(h->buf[k], p, c.storage, h->maps[k][0], h->maps[k][1]);
         h->tma = ok;
+        if (ok) {
+            void* hf = nullptr;
+            if (cudaHostAlloc(&hf, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+                cudaGetLastError();
+                cmlbm_destroy(h);
+                return fail(nullptr, CMLBM_ERR_NOMEM, "cudaHostAlloc of the pipeline flag mirror failed");
+            }
+            h->hflag = (volatile int*)hf;
+            *h->hflag = 0;
+        }
         if (!ok && c.kernel == CMLBM_KERNEL_TMA) {
             cmlbm_destroy(h);
             return fail(nullptr, CMLBM_ERR_UNSUPPORTED,
@@ -393,6 +473,12 @@ void cmlbm_destroy(cmlbm_t* h) {
     if (!h) return;
     DeviceGuard g(h->cfg.device);
     cudaStreamSynchronize(h->st);
+    if (h->inner) {
+        cudaStreamSynchronize(h->inner);
+        cudaStreamDestroy(h->inner);
+    }
+    if (h->ev_begin) cudaEventDestroy(h->ev_begin);
+    if (h->ev_interior) cudaEventDestroy(h->ev_interior);
     drop_graphs(h);
     if (h->cap) cudaStreamDestroy(h->cap);
     cudaFree(h->buf[0]);
@@ -404,6 +490,7 @@ void cmlbm_destroy(cmlbm_t* h) {
     cudaFree(h->flag);
     cudaFree(h->turb);
     cudaFree(h->ring);
+    if (h->hflag) cudaFreeHost((void*)h->hflag);
     delete h;
 }
 
@@ -427,6 +514,7 @@ size_t cmlbm_state_bytes(const cmlbm_t* h) { return h ? (size_t)h->Q * (size_t)h
 int cmlbm_set_force(cmlbm_t* h, const double uniform[3], const double* field, int where) {
     if (!h) return CMLBM_ERR_INVALID;
     DeviceGuard g(h->cfg.device);
+    if (cudaError_t ej = join_interior(h); ej != cudaSuccess) return cuda_fail(h, ej, "interior join");
     drop_graphs(h);            // the captured steps carry the old force parameters
     for (int d = 0; d < 3; ++d) {
         const double v = uniform ? uniform[d] : 0.0;
@@ -483,6 +571,7 @@ int cmlbm_init(cmlbm_t* h, const double* rho, const double* u, int where) {
     if (!h) return CMLBM_ERR_INVALID;
     if (where != CMLBM_DEVICE && where != CMLBM_HOST) return fail(h, CMLBM_ERR_INVALID, "bad `where`");
     DeviceGuard g(h->cfg.device);
+    if (cudaError_t ej = join_interior(h); ej != cudaSuccess) return cuda_fail(h, ej, "interior join");
     const size_t N = (size_t)h->p.N;
     void* dst = own(h, h->buf[h->cur]);
     auto launch = [&](const double* r, const double* v, int z0, int nzc) {
@@ -527,6 +616,9 @@ int cmlbm_step(cmlbm_t* h, int nsteps) {
     if (!h) return CMLBM_ERR_INVALID;
     if (nsteps < 0) return fail(h, CMLBM_ERR_INVALID, "nsteps must be >= 0");
     DeviceGuard g(h->cfg.device);
+    if (int rc = check_flag(h)) return rc;
+    if (cudaError_t ej = join_interior(h); ej != cudaSuccess) return cuda_fail(h, ej, "interior join");
+    const bool stepped = nsteps > 0;
     if (nsteps >= 2 && h->two_steps && !h->ring) {
         const size_t bytes = (size_t)(cm::kTwoStepRing + 2) * h->p.nx * h->p.ny * h->Q * h->esize;
         if (grid_alloc(&h->ring, bytes) != cudaSuccess) {
@@ -569,6 +661,10 @@ int cmlbm_step(cmlbm_t* h, int nsteps) {
         if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
         h->cur ^= 1;
     }
+    if (stepped) {
+        cudaError_t e = mirror_flag(h);
+        if (e != cudaSuccess) return cuda_fail(h, e, "pipeline flag copy");
+    }
     return CMLBM_OK;
 }
 
@@ -576,8 +672,44 @@ int cmlbm_step_buffers(cmlbm_t* h, const void* src, void* dst) {
     if (!h) return CMLBM_ERR_INVALID;
     if (!src || !dst || src == dst) return fail(h, CMLBM_ERR_INVALID, "src and dst must be distinct device buffers");
     DeviceGuard g(h->cfg.device);
+    if (int rc = check_flag(h)) return rc;
+    if (cudaError_t ej = join_interior(h); ej != cudaSuccess) return cuda_fail(h, ej, "interior join");
     cudaError_t e = do_step(h, src, dst);
     if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
+    e = mirror_flag(h);
+    if (e != cudaSuccess) return cuda_fail(h, e, "pipeline flag copy");
+    return CMLBM_OK;
+}
+
+int cmlbm_step_split(cmlbm_t* h) {
+    if (!h) return CMLBM_ERR_INVALID;
+    if (h->tma || h->two_steps)
+        return fail(h, CMLBM_ERR_UNSUPPORTED, "split steps use the direct or two-cells-per-thread kernel");
+    DeviceGuard g(h->cfg.device);
+    if (!h->inner) {
+        cudaError_t e = cudaStreamCreateWithFlags(&h->inner, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_begin, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_interior, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(h, e, "split-step stream");
+    }
+    const int nz = h->p.nz;
+    const void* src = h->buf[h->cur];
+    void* dst = h->buf[1 - h->cur];
+    // the interior starts after everything issued so far on the handle's stream (the previous
+    // step's boundary planes and the face exchange that followed it)
+    cudaError_t e = cudaEventRecord(h->ev_begin, h->st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->inner, h->ev_begin, 0);
+    // the boundary planes pull from the planes next to them, written by the previous interior
+    if (e == cudaSuccess) e = join_interior(h);
+    if (e == cudaSuccess) e = do_step_planes(h, src, dst, 0, 1, h->st);
+    if (e == cudaSuccess && nz > 1) e = do_step_planes(h, src, dst, nz - 1, 1, h->st);
+    if (e == cudaSuccess && nz > 2) {
+        e = do_step_planes(h, src, dst, 1, nz - 2, h->inner);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_interior, h->inner);
+        if (e == cudaSuccess) h->interior_pending = true;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "split step");
+    h->cur ^= 1;
     return CMLBM_OK;
 }
 
@@ -586,6 +718,8 @@ int cmlbm_moments_of(cmlbm_t* h, const void* state, double* rho, double* u) {
     if (!state) return fail(h, CMLBM_ERR_INVALID, "state is NULL");
     if (!rho && !u) return CMLBM_OK;
     DeviceGuard g(h->cfg.device);
+    if (int rc = check_flag(h)) return rc;
+    if (cudaError_t ej = join_interior(h); ej != cudaSuccess) return cuda_fail(h, ej, "interior join");
     cudaError_t e = do_moments(h, state, rho, u);
     if (e != cudaSuccess) return cuda_fail(h, e, "moments kernel");
     return CMLBM_OK;
@@ -597,6 +731,9 @@ int cmlbm_moments(cmlbm_t* h, double* rho, double* u, int where) {
     if (!rho && !u) return CMLBM_OK;
     DeviceGuard g(h->cfg.device);
     if (where == CMLBM_DEVICE) return cmlbm_moments_of(h, h->buf[h->cur], rho, u);
+    if (int rc = check_flag(h)) return rc;
+    if (cudaError_t ej = join_interior(h); ej != cudaSuccess) return cuda_fail(h, ej, "interior join");
+
     double* mrho = (double*)mapped_host(rho);
     double* mu = (double*)mapped_host(u);
     if ((!rho || mrho) && (!u || mu)) {
@@ -605,7 +742,7 @@ int cmlbm_moments(cmlbm_t* h, double* rho, double* u, int where) {
         if (e != cudaSuccess) return cuda_fail(h, e, "moments kernel");
         e = cudaStreamSynchronize(h->st);
         if (e != cudaSuccess) return cuda_fail(h, e, "moments");
-        return CMLBM_OK;
+        return check_flag(h);
     }
     int rc = ensure_stage(h);
     if (rc) return rc;
@@ -618,12 +755,13 @@ int cmlbm_moments(cmlbm_t* h, double* rho, double* u, int where) {
         return cuda_fail(h, e, "u download");
     e = cudaStreamSynchronize(h->st);
     if (e != cudaSuccess) return cuda_fail(h, e, "moments");
-    return CMLBM_OK;
+    return check_flag(h);
 }
 
 int cmlbm_reduce(cmlbm_t* h, double out[5]) {
     if (!h || !out) return CMLBM_ERR_INVALID;
     DeviceGuard g(h->cfg.device);
+    if (cudaError_t ej = join_interior(h); ej != cudaSuccess) return cuda_fail(h, ej, "interior join");
     h->launches += 2;
     cudaError_t e = dispatch(h, [&](auto d, auto* s) {
         using S = std::remove_pointer_t<decltype(s)>;
@@ -634,15 +772,7 @@ int cmlbm_reduce(cmlbm_t* h, double out[5]) {
     if (e != cudaSuccess) return cuda_fail(h, e, "reduction download");
     e = cudaStreamSynchronize(h->st);
     if (e != cudaSuccess) return cuda_fail(h, e, "reduction");
-    if (h->tma) {
-        int flag = 0;
-        e = cudaMemcpy(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) return cuda_fail(h, e, "pipeline flag");
-        if (flag) {
-            cudaMemset(h->flag, 0, sizeof(int));
-            return fail(h, CMLBM_ERR_CUDA, "a TMA-staged step gave up on a bounded pipeline wait");
-        }
-    }
+    if (int rc = check_flag(h)) return rc;
     for (int k = 0; k < 5; ++k)
         if (!std::isfinite(out[k])) return fail(h, CMLBM_ERR_DIVERGED, "non-finite value in the reductions");
     return CMLBM_OK;
@@ -653,11 +783,13 @@ int cmlbm_get_state(cmlbm_t* h, void* dst, size_t bytes, int where) {
     if (bytes != cmlbm_state_bytes(h)) return fail(h, CMLBM_ERR_INVALID, "bytes must equal cmlbm_state_bytes");
     if (where != CMLBM_DEVICE && where != CMLBM_HOST) return fail(h, CMLBM_ERR_INVALID, "bad `where`");
     DeviceGuard g(h->cfg.device);
+    if (int rc = check_flag(h)) return rc;
+    if (cudaError_t ej = join_interior(h); ej != cudaSuccess) return cuda_fail(h, ej, "interior join");
     cudaError_t e = cudaMemcpyAsync(dst, h->buf[h->cur], bytes, where == CMLBM_HOST ? cudaMemcpyDeviceToHost
                                                                                    : cudaMemcpyDeviceToDevice, h->st);
     if (e != cudaSuccess) return cuda_fail(h, e, "state copy");
     if (where == CMLBM_HOST && (e = cudaStreamSynchronize(h->st)) != cudaSuccess) return cuda_fail(h, e, "state copy");
-    return CMLBM_OK;
+    return where == CMLBM_HOST ? check_flag(h) : CMLBM_OK;
 }
 
 int cmlbm_set_state(cmlbm_t* h, const void* src, size_t bytes, int where) {
@@ -665,6 +797,7 @@ int cmlbm_set_state(cmlbm_t* h, const void* src, size_t bytes, int where) {
     if (bytes != cmlbm_state_bytes(h)) return fail(h, CMLBM_ERR_INVALID, "bytes must equal cmlbm_state_bytes");
     if (where != CMLBM_DEVICE && where != CMLBM_HOST) return fail(h, CMLBM_ERR_INVALID, "bad `where`");
     DeviceGuard g(h->cfg.device);
+    if (cudaError_t ej = join_interior(h); ej != cudaSuccess) return cuda_fail(h, ej, "interior join");
     cudaError_t e = cudaMemcpyAsync(h->buf[h->cur], src, bytes, where == CMLBM_HOST ? cudaMemcpyHostToDevice
                                                                                    : cudaMemcpyDeviceToDevice, h->st);
     if (e != cudaSuccess) return cuda_fail(h, e, "state copy");
@@ -677,7 +810,9 @@ int cmlbm_turbulence_force(cmlbm_t* h, double cs) {
     if (!(cs >= 0.0) || !std::isfinite(cs)) return fail(h, CMLBM_ERR_INVALID, "cs must be finite and >= 0");
     if (h->p.bc[0] || h->p.bc[1] || h->p.bc[2])
         return fail(h, CMLBM_ERR_UNSUPPORTED, "turbulence forcing needs periodic boundaries");
+    if (h->p.big) return fail(h, CMLBM_ERR_UNSUPPORTED, "turbulence forcing needs 27*N < 2^32 (32-bit element offsets)");
     DeviceGuard g(h->cfg.device);
+    if (cudaError_t ej = join_interior(h); ej != cudaSuccess) return cuda_fail(h, ej, "interior join");
     const size_t N = (size_t)h->p.N;
     if (!h->force || !h->p.has_field) drop_graphs(h);   // the steps will read a (new) force field
     if (!h->force && grid_alloc(&h->force, h->rsize * 3 * N) != cudaSuccess) {
@@ -714,6 +849,7 @@ int cmlbm_step_filtered(cmlbm_t* h, int nsteps, double cs) {
 
 static int adjoint_supported(cmlbm* h) {
     if (h->ghost) return fail(h, CMLBM_ERR_UNSUPPORTED, "the adjoint does not cover slab handles");
+    if (h->p.big) return fail(h, CMLBM_ERR_UNSUPPORTED, "the adjoint needs 27*N < 2^32 (32-bit element offsets)");
     if (h->cfg.storage != CMLBM_F64 && h->cfg.storage != CMLBM_F32)
         return fail(h, CMLBM_ERR_UNSUPPORTED, "the adjoint needs F64 or F32 storage");
     if (h->p.les || h->p.attractor != 0 || h->p.reduced)
@@ -728,6 +864,7 @@ int cmlbm_adjoint_terminal(cmlbm_t* h, const void* state, const double* dLdu, co
     int rc = adjoint_supported(h);
     if (rc) return rc;
     DeviceGuard g(h->cfg.device);
+    if (cudaError_t ej = join_interior(h); ej != cudaSuccess) return cuda_fail(h, ej, "interior join");
     ++h->launches;
     cudaError_t e;
     if (h->D == 3)
@@ -742,25 +879,37 @@ int cmlbm_adjoint_terminal(cmlbm_t* h, const void* state, const double* dLdu, co
     return CMLBM_OK;
 }
 
-int cmlbm_step_adjoint(cmlbm_t* h, const void* state, const void* lambda_in, void* lambda_out, double* dLdF) {
+static int step_adjoint(cmlbm* h, const void* state, const void* lambda_in, void* lambda_out, double* dLdF,
+                        void* seg, int acc) {
     if (!h) return CMLBM_ERR_INVALID;
     if (!state || !lambda_in || !lambda_out || !dLdF) return fail(h, CMLBM_ERR_INVALID, "NULL argument");
+    if (acc != 0 && !seg) return fail(h, CMLBM_ERR_INVALID, "seg is NULL");
     if (lambda_in == lambda_out) return fail(h, CMLBM_ERR_INVALID, "lambda_in and lambda_out must not alias");
     int rc = adjoint_supported(h);
     if (rc) return rc;
     DeviceGuard g(h->cfg.device);
+    if (cudaError_t ej = join_interior(h); ej != cudaSuccess) return cuda_fail(h, ej, "interior join");
     ++h->launches;
     cudaError_t e;
     if (h->D == 3)
         e = (h->cfg.storage == CMLBM_F64)
-                ? cm::launch_adjoint_step<3, double>(state, h->force, h->p, lambda_in, lambda_out, dLdF, h->st)
-                : cm::launch_adjoint_step<3, float>(state, h->force, h->p, lambda_in, lambda_out, dLdF, h->st);
+                ? cm::launch_adjoint_step<3, double>(state, h->force, h->p, lambda_in, lambda_out, dLdF, seg, acc, h->st)
+                : cm::launch_adjoint_step<3, float>(state, h->force, h->p, lambda_in, lambda_out, dLdF, seg, acc, h->st);
     else
         e = (h->cfg.storage == CMLBM_F64)
-                ? cm::launch_adjoint_step<2, double>(state, h->force, h->p, lambda_in, lambda_out, dLdF, h->st)
-                : cm::launch_adjoint_step<2, float>(state, h->force, h->p, lambda_in, lambda_out, dLdF, h->st);
+                ? cm::launch_adjoint_step<2, double>(state, h->force, h->p, lambda_in, lambda_out, dLdF, seg, acc, h->st)
+                : cm::launch_adjoint_step<2, float>(state, h->force, h->p, lambda_in, lambda_out, dLdF, seg, acc, h->st);
     if (e != cudaSuccess) return cuda_fail(h, e, "adjoint step kernel");
     return CMLBM_OK;
+}
+
+int cmlbm_step_adjoint(cmlbm_t* h, const void* state, const void* lambda_in, void* lambda_out, double* dLdF) {
+    return step_adjoint(h, state, lambda_in, lambda_out, dLdF, nullptr, 0);
+}
+
+int cmlbm_step_adjoint_segment(cmlbm_t* h, const void* state, const void* lambda_in, void* lambda_out, void* seg,
+                               double* dLdF, int fold) {
+    return step_adjoint(h, state, lambda_in, lambda_out, dLdF, seg, fold ? 2 : 1);
 }
 
 // ---- slab decomposition: face messages ----------------------------------------------------

@@ -17,6 +17,7 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <type_traits>
 #include <utility>
 
 namespace cm {
@@ -43,6 +44,8 @@ struct Params {
     int reduced;           // reduced compressibility (u = j / rho0)
     int has_field;         // per-cell force field present
     int pair;              // step with two cells of a row per thread (packed FP32, periodic x)
+    int big;               // Q * S >= 2^32: kernels with 64-bit element offsets
+    int z0, nzc;           // planes z0 .. z0 + nzc - 1 of a step launch (nzc = 0: all planes)
     long long N;           // cells updated (nx ny nz)
     long long S;           // elements between direction planes of a state buffer (N, or nx ny (nz + 2) on a slab)
     double uw[3][2][3];    // wall velocities [axis][side][component]
@@ -61,8 +64,10 @@ template <class R> struct PR {
     int nx, ny, nz;
     int bc[3];
     int les, vd, attractor, reduced, has_field;
+    int z0;                // first plane of a step launch (blockIdx.z counts from it)
     unsigned N;            // cells (also the stride of force and moment fields)
     unsigned S;            // direction-plane stride of a state buffer
+    unsigned long long N64, S64;   // the same as 64-bit values (kernels with 64-bit offsets)
     int wz;                // z wrap length: nz, or 0 on a slab (the ghost planes are read instead)
     R uw[3][2][3];
     R F[3];
@@ -74,8 +79,11 @@ template <class R> inline PR<R> typed(const Params& p) {
     q.nx = p.nx; q.ny = p.ny; q.nz = p.nz;
     for (int a = 0; a < 3; ++a) q.bc[a] = p.bc[a];
     q.les = p.les; q.vd = p.vd; q.attractor = p.attractor; q.reduced = p.reduced; q.has_field = p.has_field;
+    q.z0 = p.z0;
     q.N = (unsigned)p.N;
     q.S = (unsigned)p.S;
+    q.N64 = (unsigned long long)p.N;
+    q.S64 = (unsigned long long)p.S;
     q.wz = p.bc[2] == 2 ? 0 : p.nz;
     for (int a = 0; a < 3; ++a)
         for (int s = 0; s < 2; ++s)
@@ -84,6 +92,19 @@ template <class R> inline PR<R> typed(const Params& p) {
     q.tau0 = (R)p.tau0; q.omega_bulk = (R)p.omega_bulk; q.omega3 = (R)p.omega3; q.omega4 = (R)p.omega4;
     q.cs = (R)p.cs; q.vd_aplus = (R)p.vd_aplus; q.vd_utau_nu = (R)p.vd_utau_nu; q.rho0 = (R)p.rho0;
     return q;
+}
+
+// Element offsets into state buffers ([Q][S]) and [3][N] fields: 32-bit unsigned while Q * S and
+// 3 N stay below 2^32 (checked on the host), else 64-bit (BIG kernel variants). Cell indices
+// (z ny + y) nx + x are below 2^31 in both.
+template <bool BIG> using Ix = std::conditional_t<BIG, unsigned long long, unsigned>;
+template <bool BIG, class P> __host__ __device__ __forceinline__ Ix<BIG> plane_stride(const P& p) {
+    if constexpr (BIG) return p.S64;
+    else return p.S;
+}
+template <bool BIG, class P> __host__ __device__ __forceinline__ Ix<BIG> cell_count(const P& p) {
+    if constexpr (BIG) return p.N64;
+    else return p.N;
 }
 
 // reciprocal: IEEE-rounded intrinsic in FP32, plain division in FP64
@@ -134,10 +155,18 @@ template <class R> using scalar_t = typename Scalar<R>::T;
 // collision as its attractor plus the source term (the same values the general relaxation
 // gives at unit rates, with its multiplications by 1 - omega and omega left out); with GEN the
 // attractor is the factorized one where the parameters select it.
-template <bool WALLS_, bool LES_, bool FIELD_, bool GEN_, bool SIMPLE_ = false, bool UNIT_ = false> struct Feat {
-    static constexpr bool WALLS = WALLS_, LES = LES_, FIELD = FIELD_, GEN = GEN_, SIMPLE = SIMPLE_, UNIT = UNIT_;
+// FX: a UNIT collision whose force is uniform with F_y = F_z = 0 (a flow driven along x, as in
+// a channel): the source recursion keeps only its x terms, and the moments without an x
+// exponent get no source. The same values as UNIT (the terms left out are products with zero).
+// BIG: 64-bit element offsets (grids with Q * S >= 2^32).
+template <bool WALLS_, bool LES_, bool FIELD_, bool GEN_, bool SIMPLE_ = false, bool UNIT_ = false, bool BIG_ = false,
+          bool FX_ = false>
+struct Feat {
+    static constexpr bool WALLS = WALLS_, LES = LES_, FIELD = FIELD_, GEN = GEN_, SIMPLE = SIMPLE_, UNIT = UNIT_, BIG = BIG_,
+                          FX = FX_;
     static_assert(!SIMPLE_ || (!FIELD_ && !GEN_), "SIMPLE excludes force fields and the general forms");
     static_assert(!UNIT_ || !SIMPLE_, "UNIT is a forced collision");
+    static_assert(!FX_ || (UNIT_ && !FIELD_ && !GEN_), "FX is a UNIT collision with a uniform force along x");
 };
 
 // ------------------------------------------------------------------------------------------
@@ -316,14 +345,15 @@ template <class R> __device__ __forceinline__ void inv1(R& a, R& b, R& c, R u, R
 // ------------------------------------------------------------------------------------------
 // Pull with periodic wrap and half-way bounce-back; fills h (deviation populations, slot order)
 // ------------------------------------------------------------------------------------------
-template <int D, class S, bool WALLS>
+template <int D, class S, bool WALLS, bool BIG = false>
 __device__ __forceinline__ void gather_impl(const S* __restrict__ src, int x, int y, int z, const PR<typename Codec<S>::R>& p,
                                        typename Codec<S>::R (&h)[Lat<D>::Q]) {
     using R = typename Codec<S>::R;
-    // Q * S < 2^32 is checked at create. On a slab, row offsets of the ghost plane below are
-    // negative; they only occur for e_z = +1 (directions 18..26), so i * S + row stays >= 0 and
-    // the 32-bit unsigned sum is the exact offset.
-    const unsigned PS = p.S;
+    using IX = Ix<BIG>;
+    // Q * S < 2^32 is checked at create for the 32-bit variant. On a slab, row offsets of the
+    // ghost plane below are negative; they only occur for e_z = +1 (directions 18..26), so
+    // i * S + row stays >= 0 and the 32-bit unsigned sum is the exact offset.
+    const IX PS = plane_stride<BIG>(p);
     int xs[3], ys[3], zs[3];
     bool xo[3] = {false, false, false}, yo[3] = {false, false, false}, zo[3] = {false, false, false};
 #pragma unroll
@@ -364,8 +394,8 @@ __device__ __forceinline__ void gather_impl(const S* __restrict__ src, int x, in
             // issue back to back; the moving-wall term is added only where a wall was crossed
             const bool bx = xo[a], by = yo[b], bz = zo[c];
             const bool bounced = bx || by || bz;
-            const unsigned own = Lat<D>::opp(i) * PS + cell;
-            const unsigned pulled = i * PS + row[c][b] + (unsigned)xs[a];
+            const IX own = IX(Lat<D>::opp(i)) * PS + cell;
+            const IX pulled = IX(i) * PS + row[c][b] + (unsigned)xs[a];
             R d = Codec<S>::ld(src + (bounced ? own : pulled));
             constexpr int sx = (a == 2) ? 0 : 1, sy = (b == 2) ? 0 : 1, sz = (c == 2) ? 0 : 1;
             R eu = R(0);
@@ -377,7 +407,7 @@ __device__ __forceinline__ void gather_impl(const S* __restrict__ src, int x, in
             d += R(6) * eu * inv_cnt;
             h[slot<D>(i)] = d * w;
         } else {
-            h[slot<D>(i)] = Codec<S>::ld(src + (i * PS + row[c][b] + (unsigned)xs[a])) * w;
+            h[slot<D>(i)] = Codec<S>::ld(src + (IX(i) * PS + row[c][b] + (unsigned)xs[a])) * w;
         }
     });
 }
@@ -386,16 +416,16 @@ __device__ __forceinline__ void gather_impl(const S* __restrict__ src, int x, in
 // or last layer of a bounce-back axis); everywhere else the periodic pull, which never leaves the
 // box on a wall axis there. With x-rows per warp, y and z are warp-uniform, so the branch only
 // diverges on x walls.
-template <int D, class S, bool WALLS>
+template <int D, class S, bool WALLS, bool BIG = false>
 __device__ __forceinline__ void gather(const S* __restrict__ src, int x, int y, int z, const PR<typename Codec<S>::R>& p,
                                        typename Codec<S>::R (&h)[Lat<D>::Q]) {
     if constexpr (WALLS) {
         const bool near = (p.bc[0] == 1 && (x == 0 || x == p.nx - 1)) || (p.bc[1] == 1 && (y == 0 || y == p.ny - 1)) ||
                           (D == 3 && p.bc[2] == 1 && (z == 0 || z == p.nz - 1));
-        if (near) gather_impl<D, S, true>(src, x, y, z, p, h);
-        else gather_impl<D, S, false>(src, x, y, z, p, h);
+        if (near) gather_impl<D, S, true, BIG>(src, x, y, z, p, h);
+        else gather_impl<D, S, false, BIG>(src, x, y, z, p, h);
     } else {
-        gather_impl<D, S, false>(src, x, y, z, p, h);
+        gather_impl<D, S, false, BIG>(src, x, y, z, p, h);
     }
 }
 
@@ -475,7 +505,7 @@ template <int D, class R> __device__ __forceinline__ void raw_x_dev(R (&m)[Lat<D
 
 // rho - 1 and the momentum (Eqs. densitycalculation, velocitycalculation) from the raw x-line
 // moments: line l = (e_y + 1) + 3 (e_z + 1)
-template <int D, class R, bool GEN = true, bool FORCED = true>
+template <int D, class R, bool GEN = true, bool FORCED = true, bool FYZ = true>
 __device__ __forceinline__ Hydro<D, R> hydro_x(const R (&m)[Lat<D>::Q], const R F[3], const PR<scalar_t<R>>& p) {
     constexpr int NL = Lat<D>::Q / 3;
     Hydro<D, R> o;
@@ -495,8 +525,8 @@ __device__ __forceinline__ Hydro<D, R> hydro_x(const R (&m)[Lat<D>::Q], const R 
     o.drho = drho;
     if constexpr (FORCED) {
         o.jx = fma(R(0.5), F[0], jx);
-        o.jy = fma(R(0.5), F[1], jy);
-        o.jz = fma(R(0.5), F[2], jz);
+        o.jy = FYZ ? fma(R(0.5), F[1], jy) : jy;
+        o.jz = FYZ ? fma(R(0.5), F[2], jz) : jz;
     } else {
         o.jx = jx;
         o.jy = jy;
@@ -636,7 +666,7 @@ __device__ __forceinline__ void collide(R (&m)[Lat<D>::Q], const R F[3], const P
     constexpr int Q = Lat<D>::Q;
     if constexpr (DEV) raw_x_dev<D, R>(m);
     else raw_x<D, R>(m);
-    const Hydro<D, R> hy = hydro_x<D, R, FT::GEN, !FT::SIMPLE>(m, F, p);
+    const Hydro<D, R> hy = hydro_x<D, R, FT::GEN, !FT::SIMPLE, !FT::FX>(m, F, p);
     const R drho = hy.drho, rho = R(1) + hy.drho, ndrho = -hy.drho;
     const R u[3] = {hy.ux, hy.uy, hy.uz};
     central_forward_from_x<D, R>(m, u[0], u[1], u[2]);
@@ -732,11 +762,15 @@ __device__ __forceinline__ void collide(R (&m)[Lat<D>::Q], const R F[3], const P
                     constexpr int a = ex_a(t), b = ex_b(t), c = ex_c(t);
                     R s = R(0);
                     if constexpr (a > 0) s = fma(a == 2 ? Fr2[0] : Fr[0], kap[t - 1], s);
-                    if constexpr (b > 0) s = fma(b == 2 ? Fr2[1] : Fr[1], kap[t - 3], s);
-                    if constexpr (c > 0) s = fma(c == 2 ? Fr2[2] : Fr[2], kap[t - 9], s);
+                    if constexpr (b > 0 && !FT::FX) s = fma(b == 2 ? Fr2[1] : Fr[1], kap[t - 3], s);
+                    if constexpr (c > 0 && !FT::FX) s = fma(c == 2 ? Fr2[2] : Fr[2], kap[t - 9], s);
+                    constexpr bool sourced = a > 0 || (!FT::FX && (b > 0 || c > 0));
                     const R hs = R(0.5) * s;
                     const R kw = weight_cm<R, a, b, c>(cw);
-                    if constexpr (ord(t) < 2 * D) kap[t] = fma(R(0.5), s, m[t] + kw);
+                    if constexpr (ord(t) < 2 * D) {
+                        if constexpr (sourced) kap[t] = fma(R(0.5), s, m[t] + kw);
+                        else kap[t] = m[t] + kw;
+                    }
                     constexpr bool even = (a % 2 == 0) && (b % 2 == 0) && (c % 2 == 0);
                     constexpr int twos = (a == 2) + (b == 2) + (c == 2);
                     const R tp = R((T)third_pow(twos));
@@ -762,7 +796,10 @@ __device__ __forceinline__ void collide(R (&m)[Lat<D>::Q], const R F[3], const P
                         }
                     }
                     if constexpr (FT::UNIT) {
-                        m[t] = DM + hs;      // fma(0, ., fma(1, DM, hs)) of the general form
+                        // fma(0, ., fma(1, DM, hs)) of the general form: DM + s/2 rounded once (the
+                        // halving is exact), one packed instruction instead of a product and a sum
+                        if constexpr (sourced) m[t] = fma(R(0.5), s, DM);
+                        else m[t] = DM;
                     } else {
                         const R w = (ord(t) == 3) ? w3 : w4;
                         const R om = (ord(t) == 3) ? om3 : om4;
@@ -789,8 +826,8 @@ __device__ __forceinline__ void collide(R (&m)[Lat<D>::Q], const R F[3], const P
         if constexpr (D == 3) m[midx(0, 0, 1)] = fma(ndrho, u[2], hy.jz);
     } else {
         m[midx(1, 0, 0)] = fma(ndrho, u[0], fma(R(0.5), F[0], hy.jx));
-        m[midx(0, 1, 0)] = fma(ndrho, u[1], fma(R(0.5), F[1], hy.jy));
-        if constexpr (D == 3) m[midx(0, 0, 1)] = fma(ndrho, u[2], fma(R(0.5), F[2], hy.jz));
+        m[midx(0, 1, 0)] = fma(ndrho, u[1], FT::FX ? hy.jy : fma(R(0.5), F[1], hy.jy));
+        if constexpr (D == 3) m[midx(0, 0, 1)] = fma(ndrho, u[2], FT::FX ? hy.jz : fma(R(0.5), F[2], hy.jz));
     }
     // zeroth order unchanged (m[0] = drho)
 

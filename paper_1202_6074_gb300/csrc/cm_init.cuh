@@ -17,11 +17,12 @@ namespace cm {
 // holds the same values in its ghost plane). Offsets are 32-bit unsigned: a ghost row below
 // has a negative row offset only for e_z = +1 (directions 18..26), so every final offset is
 // in [0, Q*S).
-template <int D, class S>
+template <int D, class S, bool BIG = false>
 __global__ void __launch_bounds__(kBlock) k_init(S* __restrict__ dst, const typename Codec<S>::R* __restrict__ Ff,
                                                 PR<typename Codec<S>::R> p, const double* __restrict__ rho,
                                                 const double* __restrict__ u, int z0) {
     using R = typename Codec<S>::R;
+    using IX = Ix<BIG>;
     constexpr int Q = Lat<D>::Q;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -29,9 +30,10 @@ __global__ void __launch_bounds__(kBlock) k_init(S* __restrict__ dst, const type
     if (x >= p.nx || y >= p.ny) return;
     const unsigned cell = (unsigned)((z * p.ny + y) * p.nx + x);
     R F[3];
-    load_force<R>(Ff, p, cell, F);
+    load_force<R, true, BIG>(Ff, p, cell, F);
+    const IX N = cell_count<BIG>(p);
     const double r = rho ? rho[cell] : 1.0;
-    double ux = u ? u[cell] : 0.0, uy = u ? u[p.N + cell] : 0.0, uz = (u && D == 3) ? u[2 * p.N + cell] : 0.0;
+    double ux = u ? u[cell] : 0.0, uy = u ? u[N + cell] : 0.0, uz = (u && D == 3) ? u[2 * N + cell] : 0.0;
     if (p.reduced) {   // momentum rho0 u: centre the equilibrium on rho0 u / rho
         ux *= (double)p.rho0 / r;
         uy *= (double)p.rho0 / r;
@@ -67,7 +69,7 @@ __global__ void __launch_bounds__(kBlock) k_init(S* __restrict__ dst, const type
         ty[k] = sy;
         tz[k] = sz;
     }
-    const unsigned PS = p.S;
+    const IX PS = plane_stride<BIG>(p);
     sfor<Q>([&](auto I) {
         constexpr int j = decltype(I)::value;
         constexpr int a = Lat<D>::ex(j) + 1, b = Lat<D>::ey(j) + 1, c = Lat<D>::ez(j) + 1;
@@ -83,10 +85,10 @@ __global__ void __launch_bounds__(kBlock) k_init(S* __restrict__ dst, const type
             if (wy[b]) eu += ex * p.uw[1][sy][0] + ey * p.uw[1][sy][1] + ez * p.uw[1][sy][2];
             if (wz[c]) eu += ex * p.uw[2][sz][0] + ey * p.uw[2][sz][1] + ez * p.uw[2][sz][2];
             const int cnt = (int)wx[a] + (int)wy[b] + (int)wz[c];
-            Codec<S>::st(dst + (Lat<D>::opp(j) * PS + cell), d - R(6) * eu / R(cnt));
+            Codec<S>::st(dst + (IX(Lat<D>::opp(j)) * PS + cell), d - R(6) * eu / R(cnt));
         } else {
             const unsigned t = (unsigned)((tz[c] * p.ny + ty[b]) * p.nx + tx[a]);
-            Codec<S>::st(dst + (j * PS + t), d);
+            Codec<S>::st(dst + (IX(j) * PS + t), d);
         }
     });
 }
@@ -100,6 +102,12 @@ cudaError_t launch_init(void* dst, const void* Ff, const Params& p, const double
     const dim3 b = cell_block(p.nx);
     dim3 g = cell_grid(p, b);
     g.z = nzc;
+    if constexpr (D == 3) {
+        if (p.big) {
+            k_init<D, S, true><<<g, b, 0, st>>>((S*)dst, (const R*)Ff, typed<R>(p), rho, u, z0);
+            return cudaGetLastError();
+        }
+    }
     k_init<D, S><<<g, b, 0, st>>>((S*)dst, (const R*)Ff, typed<R>(p), rho, u, z0);
     return cudaGetLastError();
 }

@@ -24,14 +24,16 @@ inline dim3 cell_block(int nx) {
     while (bx < kBlock && bx < nx) bx *= 2;
     return dim3(bx, kBlock / bx, 1);
 }
+// the planes of a step launch: p.z0 .. p.z0 + step_planes(p) - 1
+inline int step_planes(const Params& p) { return p.nzc > 0 ? p.nzc : p.nz; }
 inline dim3 cell_grid(const Params& p, dim3 b) {
-    return dim3((p.nx + b.x - 1) / b.x, (p.ny + b.y - 1) / b.y, p.nz);
+    return dim3((p.nx + b.x - 1) / b.x, (p.ny + b.y - 1) / b.y, step_planes(p));
 }
 
-template <class R, bool FIELD = true>
+template <class R, bool FIELD = true, bool BIG = false>
 __device__ __forceinline__ void load_force(const R* __restrict__ Ff, const PR<R>& p, unsigned cell, R F[3]) {
     if (FIELD && p.has_field) {
-        const unsigned N = p.N;
+        const Ix<BIG> N = cell_count<BIG>(p);
         F[0] = __ldg(Ff + cell);
         F[1] = __ldg(Ff + (N + cell));
         F[2] = __ldg(Ff + (2 * N + cell));
@@ -61,19 +63,20 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S>()) k_step(const S* 
     constexpr int Q = Lat<D>::Q;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
+    const int z = (int)blockIdx.z + p.z0;
     if (x >= p.nx || y >= p.ny) return;
+    using IX = Ix<FT::BIG>;
     const unsigned cell = (unsigned)((z * p.ny + y) * p.nx + x);
-    const unsigned PS = p.S;
+    const IX PS = plane_stride<FT::BIG>(p);
     R h[Q];
-    gather<D, S, FT::WALLS>(src, x, y, z, p, h);
+    gather<D, S, FT::WALLS, FT::BIG>(src, x, y, z, p, h);
     R F[3];
-    load_force<R, FT::FIELD>(Ff, p, cell, F);
+    load_force<R, FT::FIELD, FT::BIG>(Ff, p, cell, F);
     collide<D, R, FT>(h, F, p, smagorinsky_constant<R, FT::LES>(p, y));
     sfor<Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         constexpr R iw = (R)inv_weight<D>(i);
-        Codec<S>::st(dst + (i * PS + cell), h[slot<D>(i)] * iw);
+        Codec<S>::st(dst + (IX(i) * PS + cell), h[slot<D>(i)] * iw);
     });
 }
 
@@ -83,7 +86,7 @@ template <class S, class FT>
 void launch_pair(const void* src, void* dst, const void* Ff, const Params& p, cudaStream_t st);
 
 // ---- density and velocity of the pulled field ----------------------------------------------
-template <int D, class S, bool WALLS>
+template <int D, class S, bool WALLS, bool BIG = false>
 __global__ void __launch_bounds__(kBlock) k_moments(const S* __restrict__ src, const typename Codec<S>::R* __restrict__ Ff,
                                                    PR<typename Codec<S>::R> p, double* __restrict__ rho, double* __restrict__ u,
                                                    int z0) {
@@ -93,16 +96,17 @@ __global__ void __launch_bounds__(kBlock) k_moments(const S* __restrict__ src, c
     const int z = (int)blockIdx.z + z0;
     if (x >= p.nx || y >= p.ny) return;
     const unsigned cell = (unsigned)((z * p.ny + y) * p.nx + x);
+    const Ix<BIG> N = cell_count<BIG>(p);
     R h[Lat<D>::Q];
-    gather<D, S, WALLS>(src, x, y, z, p, h);
+    gather<D, S, WALLS, BIG>(src, x, y, z, p, h);
     R F[3];
-    load_force<R>(Ff, p, cell, F);
+    load_force<R, true, BIG>(Ff, p, cell, F);
     const Hydro<D, R> hy = hydro<D, R>(h, F, p);
     if (rho) rho[cell] = 1.0 + (double)hy.drho;
     if (u) {
         u[cell] = (double)hy.ux;
-        u[p.N + cell] = (double)hy.uy;
-        u[2 * p.N + cell] = (double)hy.uz;
+        u[N + cell] = (double)hy.uy;
+        u[2 * N + cell] = (double)hy.uz;
     }
 }
 
@@ -116,8 +120,9 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// per-block partial sums of {rho, rho ux, rho uy, rho uz, rho |u|^2 / 2} into part[block*5 + k]
-template <int D, class S, bool WALLS>
+// per-block partial sums of {rho, j_x, j_y, j_z, rho |u|^2 / 2} into part[block*5 + k], with the
+// momentum j = sum fbar e + F/2 (Eq. velocitycalculation; rho u, or rho0 u in the Sec. 12 form)
+template <int D, class S, bool WALLS, bool BIG = false>
 __global__ void __launch_bounds__(kRedThreads) k_reduce_partial(const S* __restrict__ src,
                                                                const typename Codec<S>::R* __restrict__ Ff,
                                                                PR<typename Codec<S>::R> p, double* __restrict__ part) {
@@ -130,19 +135,18 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_partial(const S* __restr
         const int y = (int)(r % p.ny);
         const int z = (int)(r / p.ny);
         R h[Lat<D>::Q];
-        gather<D, S, WALLS>(src, x, y, z, p, h);
+        gather<D, S, WALLS, BIG>(src, x, y, z, p, h);
         R F[3];
-        load_force<R>(Ff, p, (unsigned)c, F);
+        load_force<R, true, BIG>(Ff, p, (unsigned)c, F);
         const Hydro<D, R> hy = hydro<D, R>(h, F, p);
         const double rho = 1.0 + (double)hy.drho;
-        const double jx = (double)hy.jx, jy = (double)hy.jy, jz = (double)hy.jz;
         const double ux = (double)hy.ux, uy = (double)hy.uy, uz = (double)hy.uz;
         acc[0] += rho;
-        acc[1] += rho * ux;
-        acc[2] += rho * uy;
-        acc[3] += rho * uz;
+        // the momentum j = sum fbar e + F/2 itself (rho u, or rho0 u with reduced compressibility)
+        acc[1] += (double)hy.jx;
+        acc[2] += (double)hy.jy;
+        acc[3] += (double)hy.jz;
         acc[4] += 0.5 * rho * (ux * ux + uy * uy + uz * uz);
-        (void)jx; (void)jy; (void)jz;
     }
     __shared__ double sh[kRedThreads / 32][5];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -244,12 +248,71 @@ void launch_step_g(const void* src, void* dst, const void* Ff, const Params& p, 
     }
     if constexpr (D == 3 && sizeof(R) == 4) {
         if (p.pair && p.omega3 == 1.0 && p.omega4 == 1.0) {
+            if constexpr (!F) {
+                if (p.F[1] == 0.0 && p.F[2] == 0.0) {      // uniform force along x only
+                    launch_step_ft<D, S, Feat<W, L, false, false, false, true, false, true>>(src, dst, Ff, p, st);
+                    return;
+                }
+            }
             launch_step_ft<D, S, Feat<W, L, F, false, false, true>>(src, dst, Ff, p, st);
             return;
         }
     }
     launch_step_ft<D, S, Feat<W, L, F, false>>(src, dst, Ff, p, st);
 }
+// The 64-bit-offset step of a D3Q27 grid: for FP32 / 16-bit storage the pair kernel with the
+// SIMPLE (unforced, unit higher rates), UNIT (forced, unit higher rates) or general-form
+// collision (the general form computes the standard collision too when neither the factorized
+// attractor nor reduced compressibility is selected); for FP64 the one-cell kernel with the
+// general form.
+template <class S, bool W, bool L, bool F>
+void launch_step_big_g(const void* src, void* dst, const void* Ff, const Params& p, cudaStream_t st) {
+    using R = typename Codec<S>::R;
+    if constexpr (sizeof(R) == 4) {
+        if (!(p.attractor != 0 || p.reduced)) {
+            if constexpr (!F) {
+                if (simple_collision(p)) {
+                    launch_pair<S, Feat<W, L, false, false, true, false, true>>(src, dst, Ff, p, st);
+                    return;
+                }
+            }
+            if (p.omega3 == 1.0 && p.omega4 == 1.0) {
+                launch_pair<S, Feat<W, L, F, false, false, true, true>>(src, dst, Ff, p, st);
+                return;
+            }
+        }
+        launch_pair<S, Feat<W, L, F, true, false, false, true>>(src, dst, Ff, p, st);
+    } else {
+        const dim3 b = cell_block(p.nx), g = cell_grid(p, b);
+        k_step<3, S, Feat<W, L, F, true, false, false, true>><<<g, b, 0, st>>>((const S*)src, (S*)dst, (const R*)Ff,
+                                                                            typed<R>(p));
+    }
+}
+template <class S>
+void launch_step_big_impl(const void* src, void* dst, const void* Ff, const Params& p, cudaStream_t st) {
+    auto by_field = [&](auto w, auto l) {
+        constexpr bool W = decltype(w)::value, L = decltype(l)::value;
+        if (p.has_field) launch_step_big_g<S, W, L, true>(src, dst, Ff, p, st);
+        else launch_step_big_g<S, W, L, false>(src, dst, Ff, p, st);
+    };
+    auto by_les = [&](auto w) {
+        if (p.les) by_field(w, std::true_type{});
+        else by_field(w, std::false_type{});
+    };
+    if (has_walls(p)) by_les(std::true_type{});
+    else by_les(std::false_type{});
+}
+
+template <class S>
+void launch_step_big(const void* src, void* dst, const void* Ff, const Params& p, cudaStream_t st) {
+    launch_step_big_impl<S>(src, dst, Ff, p, st);
+}
+// instantiated once each, in inst_big_*.cu (so that the variants compile in parallel)
+extern template void launch_step_big<double>(const void*, void*, const void*, const Params&, cudaStream_t);
+extern template void launch_step_big<float>(const void*, void*, const void*, const Params&, cudaStream_t);
+extern template void launch_step_big<__nv_bfloat16>(const void*, void*, const void*, const Params&, cudaStream_t);
+extern template void launch_step_big<__half>(const void*, void*, const void*, const Params&, cudaStream_t);
+
 template <int D, class S, bool W, bool L>
 void launch_step_f(const void* src, void* dst, const void* Ff, const Params& p, cudaStream_t st) {
     if (p.has_field) launch_step_g<D, S, W, L, true>(src, dst, Ff, p, st);
@@ -261,8 +324,18 @@ void launch_step_l(const void* src, void* dst, const void* Ff, const Params& p, 
     else launch_step_f<D, S, W, false>(src, dst, Ff, p, st);
 }
 
+// Grids with Q * S >= 2^32 (D3Q27 only): kernel variants with 64-bit element offsets
+// (instantiated in inst_big_*.cu): the pair kernel for FP32 / 16-bit storage (p.pair set at
+// create), the one-cell kernel for FP64 storage.
+
 template <int D, class S>
 cudaError_t launch_step(const void* src, void* dst, const void* Ff, const Params& p, cudaStream_t st) {
+    if constexpr (D == 3) {
+        if (p.big) {
+            launch_step_big<S>(src, dst, Ff, p, st);
+            return cudaGetLastError();
+        }
+    }
     if (has_walls(p)) launch_step_l<D, S, true>(src, dst, Ff, p, st);
     else launch_step_l<D, S, false>(src, dst, Ff, p, st);
     return cudaGetLastError();
@@ -275,10 +348,18 @@ cudaError_t launch_moments(const void* src, const void* Ff, const Params& p, dou
     const dim3 b = cell_block(p.nx);
     dim3 g = cell_grid(p, b);
     g.z = nzc;
-    if (has_walls(p))
+    if constexpr (D == 3) {
+        if (p.big) {
+            if (has_walls(p)) k_moments<D, S, true, true><<<g, b, 0, st>>>((const S*)src, (const R*)Ff, typed<R>(p), rho, u, z0);
+            else k_moments<D, S, false, true><<<g, b, 0, st>>>((const S*)src, (const R*)Ff, typed<R>(p), rho, u, z0);
+            return cudaGetLastError();
+        }
+    }
+    if (has_walls(p)) {
         k_moments<D, S, true><<<g, b, 0, st>>>((const S*)src, (const R*)Ff, typed<R>(p), rho, u, z0);
-    else
+    } else {
         k_moments<D, S, false><<<g, b, 0, st>>>((const S*)src, (const R*)Ff, typed<R>(p), rho, u, z0);
+    }
     return cudaGetLastError();
 }
 
@@ -291,10 +372,18 @@ template <int D, class S>
 cudaError_t launch_reduce(const void* src, const void* Ff, const Params& p, double* part, double* out, cudaStream_t st) {
     using R = typename Codec<S>::R;
     const int nb = reduce_blocks(p);
-    if (has_walls(p))
-        k_reduce_partial<D, S, true><<<nb, kRedThreads, 0, st>>>((const S*)src, (const R*)Ff, typed<R>(p), part);
-    else
-        k_reduce_partial<D, S, false><<<nb, kRedThreads, 0, st>>>((const S*)src, (const R*)Ff, typed<R>(p), part);
+    auto partial = [&](auto walls, auto big) {
+        k_reduce_partial<D, S, decltype(walls)::value, decltype(big)::value><<<nb, kRedThreads, 0, st>>>(
+            (const S*)src, (const R*)Ff, typed<R>(p), part);
+    };
+    using T_ = std::true_type;
+    using F_ = std::false_type;
+    bool big = false;
+    if constexpr (D == 3) {
+        big = p.big != 0;
+        if (big) has_walls(p) ? partial(T_{}, T_{}) : partial(F_{}, T_{});
+    }
+    if (!big) has_walls(p) ? partial(T_{}, F_{}) : partial(F_{}, F_{});
     k_reduce_final<<<1, kRedThreads, 0, st>>>(part, nb, out);
     return cudaGetLastError();
 }

@@ -24,9 +24,11 @@ cudaError_t launch_convert_force(const double* in, void* out, long long n, bool 
 template <int D, class R>
 cudaError_t launch_adjoint_terminal(const void* state, const void* Ff, const Params& p, const double* dLdu,
                                     const double* dLdrho, void* lambda, double* dLdF, cudaStream_t st);
+// acc: 0 = add into the FP64 dLdF, 1 = add into the segment accumulator seg (arithmetic type),
+// 2 = add into seg, then fold seg into dLdF and reset it (see adjoint.cu)
 template <int D, class R>
 cudaError_t launch_adjoint_step(const void* state, const void* Ff, const Params& p, const void* lam_in, void* lam_out,
-                                double* dLdF, cudaStream_t st);
+                                double* dLdF, void* seg, int acc, cudaStream_t st);
 
 constexpr int kReduceMaxBlocks = 1216;
 

@@ -20,11 +20,16 @@ namespace cm {
 // relaxation with a force field loses 1 % at 5 blocks and stays at 4 (at most 128 registers),
 // as do the general forms (they spill twice as much at 5) and all FP32 steps (the forced FP32
 // LES loses 7 % at 5).
+#ifndef CM_PAIR_FX_BLOCKS
+#define CM_PAIR_FX_BLOCKS (CM_PAIR_MIN_BLOCKS + 1)
+#endif
 template <class S, class FT>
 constexpr int pair_min_blocks() {
-    if constexpr (sizeof(S) == 2)
+    if constexpr (sizeof(S) == 2) {
+        if constexpr (FT::FX) return CM_PAIR_FX_BLOCKS;
         return FT::SIMPLE ? CM_PAIR_MIN_BLOCKS + 2
                           : (!FT::GEN && (!FT::FIELD || FT::UNIT) ? CM_PAIR_MIN_BLOCKS + 1 : CM_PAIR_MIN_BLOCKS);
+    }
     return CM_PAIR_MIN_BLOCKS;
 }
 
@@ -60,10 +65,12 @@ struct Ring {
 // The pair gathers return the stored deviations d (moving-wall term included), not h = w d
 // (see pair_dev).
 // RS / RD: the source / destination state is the ring (else a full buffer with stride p.S)
-template <class S, bool WALLS, bool RS = false>
+template <class S, bool WALLS, bool RS = false, bool BIG = false>
 __device__ __forceinline__ void gather_pair(const S* __restrict__ src, int x, int y, int z, const PR<float>& p, F2 (&h)[27],
                                             const Ring& ring = Ring{}) {
-    const unsigned PS = RS ? ring.stride : p.S;
+    static_assert(!(RS && BIG), "the plane ring is only used on grids with 32-bit offsets");
+    using IX = Ix<BIG>;
+    const IX PS = RS ? (IX)ring.stride : plane_stride<BIG>(p);
     const int half = p.nx >> 1;
     int xa[3], xb[3], ys[3], zs[3];
     bool yo[3] = {false, false, false}, zo[3] = {false, false, false};
@@ -107,11 +114,11 @@ __device__ __forceinline__ void gather_pair(const S* __restrict__ src, int x, in
     sfor<27>([&](auto I) {
         constexpr int i = decltype(I)::value;
         constexpr int a = Lat<3>::ex(i) + 1, b = Lat<3>::ey(i) + 1, c = Lat<3>::ez(i) + 1;
-        const unsigned base = i * PS + row[c][b];
+        const IX base = IX(i) * PS + row[c][b];
         if constexpr (WALLS) {
             const bool by = yo[b], bz = zo[c];
             const bool bounced = by || bz;
-            const unsigned own = Lat<3>::opp(i) * PS;
+            const IX own = IX(Lat<3>::opp(i)) * PS;
             const float da = Codec<S>::ld(src + (bounced ? own + cellA : base + (unsigned)xa[a]));
             const float db = Codec<S>::ld(src + (bounced ? own + cellB : base + (unsigned)xb[a]));
             constexpr int sy = (b == 2) ? 0 : 1, sz = (c == 2) ? 0 : 1;
@@ -134,10 +141,11 @@ __device__ __forceinline__ void gather_pair(const S* __restrict__ src, int x, in
 // buffer. Slot k <-> e_x = k - 1 reads columns x - e_x: c0[k] for the first cell, c1[k] for the
 // second; the e_x = 0 pair (x0, x0 + 1) is one aligned two-entry read (direction-plane
 // strides, row offsets and x0 are even).
-template <class S, bool WALLS>
+template <class S, bool WALLS, bool BIG = false>
 __device__ __forceinline__ void gather_adj(const S* __restrict__ src, int x0, int y, int z, const PR<float>& p,
                                            F2 (&h)[27]) {
-    const unsigned PS = p.S;
+    using IX = Ix<BIG>;
+    const IX PS = plane_stride<BIG>(p);
     const int c0[3] = {x0 + 1, x0, x0 == 0 ? p.nx - 1 : x0 - 1};
     const int c1[3] = {x0 + 2 == p.nx ? 0 : x0 + 2, x0 + 1, x0};
     int ys[3], zs[3];
@@ -165,11 +173,11 @@ __device__ __forceinline__ void gather_adj(const S* __restrict__ src, int x0, in
     sfor<27>([&](auto I) {
         constexpr int i = decltype(I)::value;
         constexpr int a = Lat<3>::ex(i) + 1, b = Lat<3>::ey(i) + 1, c = Lat<3>::ez(i) + 1;
-        const unsigned base = i * PS + row[c][b];
+        const IX base = IX(i) * PS + row[c][b];
         if constexpr (WALLS) {
             const bool by = yo[b], bz = zo[c];
             const bool bounced = by || bz;
-            const unsigned back = Lat<3>::opp(i) * PS + own;     // the cells' own reflected entries
+            const IX back = IX(Lat<3>::opp(i)) * PS + own;       // the cells' own reflected entries
             float2 d;
             if constexpr (a == 1) {
                 d = Codec<S>::ld2(src + (bounced ? back : base + (unsigned)x0));
@@ -200,33 +208,35 @@ __global__ void __launch_bounds__(kBlock, pair_min_blocks<S, FT>()) k_step_pair(
     const int half = p.nx >> 1;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = (RS || RD) ? (int)blockIdx.z + ring.z0 : (int)blockIdx.z;
+    const int z = (int)blockIdx.z + ring.z0;     // the ring's group, or the launch's first plane
     if (x >= half || y >= p.ny) return;
     static_assert(!ADJ || (!RS && !RD), "adjacent cells only between full state buffers");
     // global cells (force field) and the destination cells
     const int xa = ADJ ? 2 * x : x;
     const unsigned cellA = (unsigned)((z * p.ny + y) * p.nx + xa), cellB = cellA + (ADJ ? 1u : (unsigned)half);
     const unsigned dA = RD ? ring.plane(z) + (unsigned)(y * p.nx + x) : cellA, dB = dA + (unsigned)half;
-    const unsigned PS = RD ? ring.stride : p.S;
+    static_assert(!FT::BIG || (!RS && !RD), "the plane ring is only used on grids with 32-bit offsets");
+    using IX = Ix<FT::BIG>;
+    const IX PS = RD ? (IX)ring.stride : plane_stride<FT::BIG>(p);
     F2 h[27];
     if constexpr (ADJ) {
         if constexpr (FT::WALLS) {
             const bool near = (p.bc[1] == 1 && (y == 0 || y == p.ny - 1)) || (p.bc[2] == 1 && (z == 0 || z == p.nz - 1));
-            if (near) gather_adj<S, true>(src, xa, y, z, p, h);
-            else gather_adj<S, false>(src, xa, y, z, p, h);
+            if (near) gather_adj<S, true, FT::BIG>(src, xa, y, z, p, h);
+            else gather_adj<S, false, FT::BIG>(src, xa, y, z, p, h);
         } else {
-            gather_adj<S, false>(src, xa, y, z, p, h);
+            gather_adj<S, false, FT::BIG>(src, xa, y, z, p, h);
         }
     } else if constexpr (FT::WALLS) {
         const bool near = (p.bc[1] == 1 && (y == 0 || y == p.ny - 1)) || (p.bc[2] == 1 && (z == 0 || z == p.nz - 1));
-        if (near) gather_pair<S, true, RS>(src, x, y, z, p, h, ring);
-        else gather_pair<S, false, RS>(src, x, y, z, p, h, ring);
+        if (near) gather_pair<S, true, RS, FT::BIG>(src, x, y, z, p, h, ring);
+        else gather_pair<S, false, RS, FT::BIG>(src, x, y, z, p, h, ring);
     } else {
-        gather_pair<S, false, RS>(src, x, y, z, p, h, ring);
+        gather_pair<S, false, RS, FT::BIG>(src, x, y, z, p, h, ring);
     }
     F2 F[3];
     if (FT::FIELD && p.has_field) {
-        const unsigned N = p.N;
+        const IX N = cell_count<FT::BIG>(p);
         if constexpr (ADJ) {
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
@@ -258,8 +268,8 @@ __global__ void __launch_bounds__(kBlock, pair_min_blocks<S, FT>()) k_step_pair(
             Codec<S>::st(dst + dA + (size_t)PS * i, v.v.x);
             Codec<S>::st(dst + dB + (size_t)PS * i, v.v.y);
         } else {
-            Codec<S>::st(dst + (i * PS + dA), v.v.x);
-            Codec<S>::st(dst + (i * PS + dB), v.v.y);
+            Codec<S>::st(dst + (IX(i) * PS + dA), v.v.x);
+            Codec<S>::st(dst + (IX(i) * PS + dB), v.v.y);
         }
     });
 }
@@ -268,18 +278,20 @@ template <class S, class FT>
 void launch_pair(const void* src, void* dst, const void* Ff, const Params& p, cudaStream_t st) {
     const int half = p.nx / 2;
     const dim3 b = cell_block(half);
-    const dim3 g((half + b.x - 1) / b.x, (p.ny + b.y - 1) / b.y, p.nz);
+    const dim3 g((half + b.x - 1) / b.x, (p.ny + b.y - 1) / b.y, step_planes(p));
+    Ring planes{};
+    planes.z0 = p.z0;
     // adjacent cells need both buffers aligned to two entries (buffers passed in by the caller
     // may be offset); the force field is the library's own allocation
     if constexpr (pair_adjacent<S, FT>()) {
         const uintptr_t two = 2 * sizeof(S);
         if ((uintptr_t)src % two == 0 && (uintptr_t)dst % two == 0) {
             k_step_pair<S, FT, false, false, true><<<g, b, 0, st>>>((const S*)src, (S*)dst, (const float*)Ff,
-                                                                     typed<float>(p), Ring{});
+                                                                     typed<float>(p), planes);
             return;
         }
     }
-    k_step_pair<S, FT><<<g, b, 0, st>>>((const S*)src, (S*)dst, (const float*)Ff, typed<float>(p), Ring{});
+    k_step_pair<S, FT><<<g, b, 0, st>>>((const S*)src, (S*)dst, (const float*)Ff, typed<float>(p), planes);
 }
 
 // Two steps per pass (temporal blocking through the L2 cache). Steps t -> t+1 -> t+2 from the
@@ -339,7 +351,8 @@ int launch_pair_two_steps(const void* A, void* C, void* ring, int P, int slots, 
     template void launch_pair<S, Feat<true, false, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);  \
     template void launch_pair<S, Feat<true, true, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);
 
-// the forced standard collision with unit higher-order rates (the default rates)
+// the forced standard collision with unit higher-order rates (the default rates), and its form for
+// a uniform force along x (FX)
 #define CM_PAIR_INSTANTIATE_UNIT(S)                                                                         \
     template void launch_pair<S, Feat<false, false, false, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t); \
     template void launch_pair<S, Feat<false, false, true, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);  \
@@ -348,7 +361,11 @@ int launch_pair_two_steps(const void* A, void* C, void* ring, int P, int slots, 
     template void launch_pair<S, Feat<true, false, false, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);  \
     template void launch_pair<S, Feat<true, false, true, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);   \
     template void launch_pair<S, Feat<true, true, false, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);   \
-    template void launch_pair<S, Feat<true, true, true, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);
+    template void launch_pair<S, Feat<true, true, true, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t); \
+    template void launch_pair<S, Feat<false, false, false, false, false, true, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t); \
+    template void launch_pair<S, Feat<false, true, false, false, false, true, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t); \
+    template void launch_pair<S, Feat<true, false, false, false, false, true, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t); \
+    template void launch_pair<S, Feat<true, true, false, false, false, true, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);
 
 // the general forms with unit higher-order rates
 #define CM_PAIR_INSTANTIATE_GEN_UNIT(S)                                                                     \

@@ -1,0 +1,6 @@
+// Step kernels with 64-bit element offsets (grids with Q * N >= 2^32) for float storage.
+#include "cm_pair.cuh"
+
+namespace cm {
+template void launch_step_big<float>(const void*, void*, const void*, const Params&, cudaStream_t);
+}  // namespace cm

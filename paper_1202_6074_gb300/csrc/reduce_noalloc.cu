@@ -1,8 +1,8 @@
 // Allocation-free variant of the FP64 diagnostics reduction (cmlbm_reduce_noalloc).
 //
-// Callers such as code running inside a CUDA graph that is being captured, a host that
-// cannot allocate device memory once set up, or a memory-pool-managed runtime that forbids
-// outside cudaMalloc, need the reductions without an allocation. This entry point needs no
+// Callers such as a host that cannot allocate device memory once set up (a fixed memory
+// budget), or a runtime whose memory pool owns the device memory and forbids outside cudaMalloc,
+// need the reductions without an allocation. This entry point needs no
 // handle and allocates nothing: its per-block partial sums live in the file-scope device array
 // `g_reduce_scratch` below (kNoAllocMaxBlocks x 5 doubles = 640 KiB, held by every GPU that
 // loads the library until the process exits). Each block of 256 threads covers 1024 cells, so
@@ -52,9 +52,9 @@ __global__ void __launch_bounds__(kNoAllocThreads) k_reduce_blocks(const S* __re
         const double rho = 1.0 + (double)hy.drho;
         const double ux = (double)hy.ux, uy = (double)hy.uy, uz = (double)hy.uz;
         acc[0] += rho;
-        acc[1] += rho * ux;
-        acc[2] += rho * uy;
-        acc[3] += rho * uz;
+        acc[1] += (double)hy.jx;
+        acc[2] += (double)hy.jy;
+        acc[3] += (double)hy.jz;
         acc[4] += 0.5 * rho * (ux * ux + uy * uy + uz * uz);
     }
     __shared__ double sh[kNoAllocThreads / 32][5];
@@ -114,7 +114,8 @@ cudaError_t launch_noalloc(const void* state, const void* Ff, const Params& p, d
     return cudaGetLastError();
 }
 
-// Device address of g_reduce_scratch, looked up once per device with that device current.
+// Device address of g_reduce_scratch, looked up once per device with that device current and
+// kept for the life of the process (a cudaDeviceReset invalidates it; the header says so).
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mutex;
 void* g_scratch_addr[kMaxDevices] = {};

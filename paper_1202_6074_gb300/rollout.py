@@ -7,8 +7,10 @@ torch.autograd.Function. Its backward runs the adjoint kernels of libcmlbm.so:
   forward   s_{t+1} = step(s_t, F); a checkpoint is kept every ``segment`` steps
   backward  lambda_T = pull^T (du_T/dg)^T dL/du_T           (cmlbm_adjoint_terminal)
             for each segment, last first: recompute its states from the checkpoint
-            (cmlbm_step_buffers), then lambda_t = J_t^T lambda_{t+1} and dL/dF += ...
-            (cmlbm_step_adjoint), with dL/dF accumulated in FP64.
+            (cmlbm_step_buffers; the last segment's states are kept from the forward sweep),
+            then lambda_t = J_t^T lambda_{t+1} and dL/dF += ... (cmlbm_step_adjoint_segment):
+            the force gradient of a segment is summed in the arithmetic precision and added
+            into the FP64 dL/dF once per segment.
 Memory: ceil(steps / segment) checkpoints plus one segment of states, instead of all steps.
 The initial state s0 is an input held fixed (its own dependence on F is not differentiated).
 """
@@ -23,17 +25,31 @@ class _Rollout(torch.autograd.Function):
     @staticmethod
     def forward(ctx, F, solver, s0, steps, segment):
         solver.set_force((0.0, 0.0, 0.0), F.detach())
+        nseg = (steps + segment - 1) // segment
+        last = (nseg - 1) * segment          # first step of the last segment
         ckpts = [s0.detach().clone()]
-        cur = s0.detach().clone()
-        nxt = solver.new_state()
+        # the states of the last segment, s_last .. s_(steps-1), are written by the forward steps
+        # into buffers that are kept for the backward sweep (which then need not recompute them)
+        tail = [ckpts[0]] if last == 0 else []
+        cur = ckpts[0]
+        ping = [solver.new_state(), solver.new_state()]
         for t in range(steps):
+            if t + 1 >= last and t + 1 > 0:
+                nxt = solver.new_state()
+            else:
+                nxt = ping[t % 2]
             solver.step_buffers(cur, nxt)
-            cur, nxt = nxt, cur
-            if (t + 1) % segment == 0 and t + 1 < steps:
+            cur = nxt
+            if t + 1 < last and (t + 1) % segment == 0:
                 ckpts.append(cur.clone())
+            if last <= t + 1 < steps:
+                if t + 1 == last:
+                    ckpts.append(cur)
+                tail.append(cur)
         _, u = solver.moments(state=cur)
         ctx.solver, ctx.steps, ctx.segment = solver, steps, segment
         ctx.ckpts = ckpts
+        ctx.tail = tail
         ctx.final = cur
         ctx.F = F.detach()
         return u
@@ -47,20 +63,28 @@ class _Rollout(torch.autograd.Function):
         lam = torch.empty(shape, dtype=solver.real_dtype, device=dev)
         lam2 = torch.empty_like(lam)
         dLdF = torch.zeros((3,) + solver.shape, dtype=torch.float64, device=dev)
+        # the force gradient of the steps of one segment is summed in the arithmetic precision and
+        # folded into the FP64 dLdF at the segment's first step
+        seg = torch.zeros((3,) + solver.shape, dtype=solver.real_dtype, device=dev)
         solver.adjoint_terminal(ctx.final, gu.detach().to(torch.float64).contiguous(), lam, dLdF)
         nseg = (steps + segment - 1) // segment
         buf = [None] * segment
         for k in reversed(range(nseg)):
             start, end = k * segment, min((k + 1) * segment, steps)
-            buf[0] = ctx.ckpts[k]
-            for t in range(start + 1, end):
-                j = t - start
-                if buf[j] is None or buf[j] is buf[0]:
-                    buf[j] = solver.new_state()
-                solver.step_buffers(buf[j - 1], buf[j])
+            if k == nseg - 1:
+                states = ctx.tail
+            else:
+                buf[0] = ctx.ckpts[k]
+                for t in range(start + 1, end):
+                    j = t - start
+                    if buf[j] is None or buf[j] is buf[0]:
+                        buf[j] = solver.new_state()
+                    solver.step_buffers(buf[j - 1], buf[j])
+                states = buf
             for t in reversed(range(start, end)):
-                solver.step_adjoint(buf[t - start], lam, lam2, dLdF)
+                solver.step_adjoint_segment(states[t - start], lam, lam2, seg, dLdF, fold=(t == start))
                 lam, lam2 = lam2, lam
+        ctx.tail = None
         return dLdF, None, None, None, None
 
 

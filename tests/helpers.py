@@ -93,3 +93,42 @@ def pull_sampled(state_dev, cells, name, bc, wall_velocity):
 def zero_walls():
     z = [0.0, 0.0, 0.0]
     return [[z, z], [z, z], [z, z]]
+
+
+# Trajectory bounds against the FP64 oracle, on the velocity fluctuation u - U about the
+# background U (the stricter measure; equal to rel-L2(u) at rest): 1e-5 for FP32 and 2e-3, the
+# stated target, for 16-bit storage.
+#
+# A 16-bit run is also compared with the oracle whose stored state is rounded to the same format
+# after every step (OracleSim(storage=...)): that oracle's own error against FP64 is what the
+# storage format costs. The GPU run and that oracle round different values (FP32 against FP64
+# arithmetic), so their rounding decisions decorrelate within a few steps, but their errors
+# against FP64 must be statistically the same: |err - err_format| <= 20 % of err_format says
+# the kernels add nothing the format does not. BF16 keeps 8 significant bits; where the format
+# alone exceeds 2e-3 (a background flow, whose deviations the stored values carry too, or the
+# 100-step LES runs), BF16 misses the target and BF16_MISS holds the bound asserted instead,
+# next to the measured values.
+TARGET = {"f32": 1e-5, "f16": 2e-3, "bf16": 2e-3}
+BF16_MISS = {                 # case: (asserted bound, measured GPU error, measured format error)
+    "tgv_moving_frame": (6e-3, 4.30e-3, 4.31e-3),
+    "hit_les": (3.5e-3, 2.45e-3, 2.45e-3),
+    "channel": (3e-3, 2.18e-3, 2.18e-3),
+}
+FORMAT_AGREEMENT = 0.2
+
+
+def check_16bit(storage, case, err, err_format=None):
+    """Assert the trajectory bounds for a storage type (see the comment above)."""
+    if storage == "f32":
+        assert err < TARGET["f32"], f"f32 {case}: rel-L2 = {err:.3e}"
+        return
+    assert err_format is not None
+    assert abs(err - err_format) <= FORMAT_AGREEMENT * err_format, \
+        f"{storage} {case}: GPU {err:.3e} against the {storage} format alone {err_format:.3e}"
+    if storage == "bf16" and case in BF16_MISS:
+        bound = BF16_MISS[case][0]
+        assert err < bound, f"BF16 {case}: rel-L2 = {err:.3e} (bound {bound:.1e})"
+        assert err_format > TARGET["bf16"], f"BF16 {case} now meets the 2e-3 target ({err:.3e}): update BF16_MISS"
+        print(f"BF16 misses the 2e-3 target on {case}: rel-L2 = {err:.3e} (the storage format alone: {err_format:.3e})")
+    else:
+        assert err < TARGET[storage], f"{storage} {case}: rel-L2 = {err:.3e}"

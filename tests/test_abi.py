@@ -51,7 +51,7 @@ def test_config_struct_size_matches(lib):
     (dict(van_driest=(26.0, 1.0), smagorinsky_cs=0.1), "walls in y"),
     (dict(van_driest=(26.0, 1.0), bc=("periodic", "bounceback", "periodic")), "smagorinsky_cs"),
     (dict(nx=2048, ny=1024, nz=1024), "2^31"),
-    (dict(nx=1024, ny=1024, nz=200), "2^32"),
+    (dict(lattice="D2Q9", nx=65536, ny=8192, nz=1), "9*nx*ny < 2^32"),
     (dict(attractor=3), "attractor"),
     (dict(reduced_compressibility=True, rho0=0.0), "rho0"),
     (dict(bc=("halo", "periodic", "periodic")), "CMLBM_HALO on z"),
@@ -67,6 +67,24 @@ def test_invalid_configs_are_rejected_without_a_gpu(lib, kw, msg):
     assert rc == lib.ERR_INVALID
     assert h.value is None
     assert msg in so.cmlbm_last_error(None).decode()
+
+
+@pytest.mark.parametrize("kw", [
+    # D3Q27 with 27 N >= 2^32 runs 64-bit-offset variants of the pair kernel (FP32 / 16-bit: periodic
+    # x, nx a multiple of 64) or of the one-cell kernel (FP64); everything else is refused
+    dict(nx=1024, ny=1024, nz=200, bc=("bounceback", "periodic", "periodic")),
+    dict(nx=1000, ny=1024, nz=200),
+    dict(nx=1024, ny=1024, nz=200, kernel="tma"),
+    dict(nx=1024, ny=1024, nz=200, kernel="pair_two_steps"),
+    dict(nx=1024, ny=1024, nz=200, kernel="direct"),
+])
+def test_large_grid_forms_without_64bit_variants_are_unsupported(lib, kw):
+    c = lib.make_config(**kw)
+    h = ctypes.c_void_p()
+    so = lib.load()
+    assert so.cmlbm_create(ctypes.byref(c), ctypes.byref(h)) == lib.ERR_UNSUPPORTED
+    assert h.value is None
+    assert "2^32" in so.cmlbm_last_error(None).decode()
 
 
 def test_tma_on_a_slab_is_unsupported_without_a_gpu(lib):

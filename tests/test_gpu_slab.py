@@ -86,16 +86,19 @@ def _slabs(cm, c, rho, u, F, k):
     return out
 
 
+@pytest.mark.parametrize("overlap", [False, True])
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("k", [1, 2, 3])
-def test_slabs_reproduce_the_single_domain_bitwise(cm, name, k):
+def test_slabs_reproduce_the_single_domain_bitwise(cm, name, k, overlap):
+    """overlap: split steps (boundary planes on the handle's stream, interior planes on the
+    library's own) with the face exchange issued while the interior runs."""
     c = CASES[name]
     rho, u, F = _fields()
     ref = _single(cm, c, rho, u, F)
     slabs = _slabs(cm, c, rho, u, F, k)
     assert slabs[0].state_shape[1] == slabs[0].shape[0] + 2
     ref.step(STEPS)
-    run = SL.SlabRun(slabs, SL.LocalExchange(slabs))
+    run = SL.SlabRun(slabs, SL.LocalExchange(slabs), overlap=overlap)
     run.step(STEPS)
     torch.cuda.synchronize()
     s_ref = ref.get_state()
@@ -227,3 +230,26 @@ def test_slabs_with_the_two_cell_kernel(cm, storage, force):
     assert torch.equal(own.view(torch.uint8), ref.get_state().view(torch.uint8))
     for s in slabs + [ref]:
         s.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16", "f64"])
+def test_split_step_equals_step_on_a_single_domain(cm, storage):
+    """cmlbm_step_split on an ordinary handle: the same state as cmlbm_step, bit for bit, and the
+    calls that follow it see the interior planes."""
+    c = dict(storage=storage, tau=0.6, omega_bulk=1.0, field=True)
+    rho, u, F = _fields(7)
+    a = _single(cm, c, rho, u, F)
+    b = _single(cm, c, rho, u, F)
+    for _ in range(5):
+        a.step_split()
+    b.step(5)
+    assert torch.equal(a.get_state().view(torch.uint8), b.get_state().view(torch.uint8))
+    assert a.reduce() == b.reduce()
+    a.step_split()
+    ra, ua = a.moments()
+    b.step(1)
+    rb, ub = b.moments()
+    assert torch.equal(ra, rb) and torch.equal(ua, ub)
+    a.close()
+    b.close()
+
