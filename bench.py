@@ -60,6 +60,10 @@ def parse():
     ap.add_argument("--flow", default="tgv", choices=["tgv", "hit"],
                     help="timed workload: the Taylor-Green vortex (headline) or the forced isotropic "
                          "turbulence LES (force field, Cs = 0.1) on the same n^3 box")
+    ap.add_argument("--only", default=None, choices=["channel", "hit"],
+                    help="run only this form (16-bit storage by --storage, shape by --shape) and print its "
+                         "MLUPS; for profiling captures of one kernel variant")
+    ap.add_argument("--shape", default=None, help="nx,ny,nz of the --only form")
     ap.add_argument("--kernel", default="auto", choices=["auto", "direct", "pair", "pair_two_steps", "tma"],
                     help="step kernel: the library's choice (auto), one cell per thread (direct), two cells "
                          "per thread in packed FP32 (pair), or rows staged by TMA (tma)")
@@ -685,8 +689,34 @@ class Dist0:
         pass
 
 
+def only_form(args):
+    """One form at a chosen shape (a profiling aid): --warmup steps, then --form-steps timed."""
+    import __graft_entry__ as G
+
+    G.build()
+    from paper_1202_6074_gb300 import cmlbm as cm
+
+    st = "bf16" if args.storage == "f32" and args.only == "channel" else args.storage
+    if args.only == "channel":
+        nx, ny, nz = (int(v) for v in (args.shape or "1024,256,256").split(","))
+        ms, _ = run_channel(cm, st, args.form_steps, args.warmup, Dist0(), nx=nx, ny=ny, nz=nz)
+        bpc = BYTES_PER_CELL[("D3Q27", st)]
+    else:
+        nx, ny, nz = (int(v) for v in (args.shape or "512,512,512").split(","))
+        assert nx == ny == nz, "the forced isotropic turbulence form runs on a cube"
+        ms, _ = run_hit_les(cm, nx, st, args.form_steps, args.warmup, Dist0())
+        bpc = BYTES_PER_CELL[("D3Q27", st)] + 12
+    N = nx * ny * nz
+    mlups = N * args.form_steps / (ms / 1e3) / 1e6
+    print(json.dumps({"form": args.only, "shape": [nx, ny, nz], "storage": st, "steps": args.form_steps,
+                      "MLUPS": mlups, "GBs": bpc * mlups / 1e3, "bytes_per_cell": bpc}))
+
+
 def main():
     args = parse()
+    if args.only:
+        only_form(args)
+        return
     dist = Dist()
     try:
         if args.impl == "reference":

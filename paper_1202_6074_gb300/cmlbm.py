@@ -85,7 +85,7 @@ def load():
         "cmlbm_set_force": (I, [P, D, P, I]),
         "cmlbm_init": (I, [P, P, P, I]),
         "cmlbm_step": (I, [P, I]),
-        "cmlbm_step_split": (I, [P]),
+        "cmlbm_step_split": (I, [P, I]),
         "cmlbm_step_buffers": (I, [P, P, P]),
         "cmlbm_moments": (I, [P, P, P, I]),
         "cmlbm_moments_of": (I, [P, P, P, P]),
@@ -254,10 +254,11 @@ class Solver:
     def step(self, n=1):
         self._check(self.lib.cmlbm_step(self.h, int(n)))
 
-    def step_split(self):
+    def step_split(self, parts=3):
         """One step with the boundary planes on the handle's stream and the interior on the
-        library's own (cmlbm_step_split): a face exchange issued next overlaps the interior."""
-        self._check(self.lib.cmlbm_step_split(self.h))
+        library's own (cmlbm_step_split): a face exchange issued next overlaps the interior.
+        parts = 1 (boundary) and then 2 (interior) issue the two parts in two calls."""
+        self._check(self.lib.cmlbm_step_split(self.h, int(parts)))
 
     def turbulence_force(self, cs):
         """Set the force field to rho a' from the Smagorinsky closure (filtered equation)."""

@@ -76,6 +76,7 @@ struct cmlbm {
     cudaStream_t inner = nullptr;
     cudaEvent_t ev_begin = nullptr, ev_interior = nullptr;
     bool interior_pending = false;
+    bool boundary_done = false;    // the boundary part of a split step was issued, its interior not yet
 };
 
 namespace {
@@ -617,6 +618,7 @@ int cmlbm_step(cmlbm_t* h, int nsteps) {
     if (nsteps < 0) return fail(h, CMLBM_ERR_INVALID, "nsteps must be >= 0");
     DeviceGuard g(h->cfg.device);
     if (int rc = check_flag(h)) return rc;
+    if (h->boundary_done) return fail(h, CMLBM_ERR_INVALID, "a split step waits for its interior part");
     if (cudaError_t ej = join_interior(h); ej != cudaSuccess) return cuda_fail(h, ej, "interior join");
     const bool stepped = nsteps > 0;
     if (nsteps >= 2 && h->two_steps && !h->ring) {
@@ -681,13 +683,22 @@ int cmlbm_step_buffers(cmlbm_t* h, const void* src, void* dst) {
     return CMLBM_OK;
 }
 
-int cmlbm_step_split(cmlbm_t* h) {
+int cmlbm_step_split(cmlbm_t* h, int parts) {
     if (!h) return CMLBM_ERR_INVALID;
+    if (parts < CMLBM_SPLIT_BOUNDARY || parts > CMLBM_SPLIT_BOTH) return fail(h, CMLBM_ERR_INVALID, "bad parts");
     if (h->tma || h->two_steps)
         return fail(h, CMLBM_ERR_UNSUPPORTED, "split steps use the direct or two-cells-per-thread kernel");
+    if (parts == CMLBM_SPLIT_INTERIOR && !h->boundary_done)
+        return fail(h, CMLBM_ERR_INVALID, "the interior part of a split step needs its boundary part first");
+    if (parts != CMLBM_SPLIT_INTERIOR && h->boundary_done)
+        return fail(h, CMLBM_ERR_INVALID, "the interior part of the previous split step is still to come");
     DeviceGuard g(h->cfg.device);
     if (!h->inner) {
-        cudaError_t e = cudaStreamCreateWithFlags(&h->inner, cudaStreamNonBlocking);
+        // the interior runs at the lowest stream priority, so that the boundary planes and the
+        // face exchange, issued on a stream of higher priority, are dispatched ahead of its blocks
+        int lowest = 0, highest = 0;
+        cudaError_t e = cudaDeviceGetStreamPriorityRange(&lowest, &highest);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->inner, cudaStreamNonBlocking, lowest);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_begin, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_interior, cudaEventDisableTiming);
         if (e != cudaSuccess) return cuda_fail(h, e, "split-step stream");
@@ -695,21 +706,28 @@ int cmlbm_step_split(cmlbm_t* h) {
     const int nz = h->p.nz;
     const void* src = h->buf[h->cur];
     void* dst = h->buf[1 - h->cur];
-    // the interior starts after everything issued so far on the handle's stream (the previous
-    // step's boundary planes and the face exchange that followed it)
-    cudaError_t e = cudaEventRecord(h->ev_begin, h->st);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->inner, h->ev_begin, 0);
-    // the boundary planes pull from the planes next to them, written by the previous interior
-    if (e == cudaSuccess) e = join_interior(h);
-    if (e == cudaSuccess) e = do_step_planes(h, src, dst, 0, 1, h->st);
-    if (e == cudaSuccess && nz > 1) e = do_step_planes(h, src, dst, nz - 1, 1, h->st);
-    if (e == cudaSuccess && nz > 2) {
-        e = do_step_planes(h, src, dst, 1, nz - 2, h->inner);
-        if (e == cudaSuccess) e = cudaEventRecord(h->ev_interior, h->inner);
-        if (e == cudaSuccess) h->interior_pending = true;
+    cudaError_t e = cudaSuccess;
+    if (parts & CMLBM_SPLIT_BOUNDARY) {
+        // the interior starts after everything issued so far on the handle's stream (the
+        // previous step's boundary planes and the face exchange that followed it)
+        e = cudaEventRecord(h->ev_begin, h->st);
+        // the boundary planes pull from the planes next to them, written by the previous interior
+        if (e == cudaSuccess) e = join_interior(h);
+        if (e == cudaSuccess) e = do_step_planes(h, src, dst, 0, 1, h->st);
+        if (e == cudaSuccess && nz > 1) e = do_step_planes(h, src, dst, nz - 1, 1, h->st);
+        h->boundary_done = e == cudaSuccess;
+    }
+    if (e == cudaSuccess && (parts & CMLBM_SPLIT_INTERIOR)) {
+        e = cudaStreamWaitEvent(h->inner, h->ev_begin, 0);
+        if (e == cudaSuccess && nz > 2) {
+            e = do_step_planes(h, src, dst, 1, nz - 2, h->inner);
+            if (e == cudaSuccess) e = cudaEventRecord(h->ev_interior, h->inner);
+            if (e == cudaSuccess) h->interior_pending = true;
+        }
+        h->boundary_done = false;
+        if (e == cudaSuccess) h->cur ^= 1;
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "split step");
-    h->cur ^= 1;
     return CMLBM_OK;
 }
 
@@ -796,6 +814,7 @@ int cmlbm_set_state(cmlbm_t* h, const void* src, size_t bytes, int where) {
     if (!h || !src) return CMLBM_ERR_INVALID;
     if (bytes != cmlbm_state_bytes(h)) return fail(h, CMLBM_ERR_INVALID, "bytes must equal cmlbm_state_bytes");
     if (where != CMLBM_DEVICE && where != CMLBM_HOST) return fail(h, CMLBM_ERR_INVALID, "bad `where`");
+    if (h->boundary_done) return fail(h, CMLBM_ERR_INVALID, "a split step waits for its interior part");
     DeviceGuard g(h->cfg.device);
     if (cudaError_t ej = join_interior(h); ej != cudaSuccess) return cuda_fail(h, ej, "interior join");
     cudaError_t e = cudaMemcpyAsync(h->buf[h->cur], src, bytes, where == CMLBM_HOST ? cudaMemcpyHostToDevice

@@ -72,6 +72,7 @@ template <class R> struct PR {
     R uw[3][2][3];
     R F[3];
     R tau0, omega_bulk, omega3, omega4, cs, vd_aplus, vd_utau_nu, rho0;
+    R omega_nu;            // 1 / tau0, IEEE-rounded on the host (used by the FP64 collision)
 };
 
 template <class R> inline PR<R> typed(const Params& p) {
@@ -91,6 +92,7 @@ template <class R> inline PR<R> typed(const Params& p) {
     for (int d = 0; d < 3; ++d) q.F[d] = (R)p.F[d];
     q.tau0 = (R)p.tau0; q.omega_bulk = (R)p.omega_bulk; q.omega3 = (R)p.omega3; q.omega4 = (R)p.omega4;
     q.cs = (R)p.cs; q.vd_aplus = (R)p.vd_aplus; q.vd_utau_nu = (R)p.vd_utau_nu; q.rho0 = (R)p.rho0;
+    q.omega_nu = (R)(1.0 / p.tau0);
     return q;
 }
 
@@ -707,6 +709,11 @@ __device__ __forceinline__ void collide(R (&m)[Lat<D>::Q], const R F[3], const P
             tau = R(0.5) * (tau + sqrt(fma(tau, tau, k * Qn * irho)));
         }
         wnu = rcp(tau);
+    } else if constexpr (std::is_same_v<R, double>) {
+        // the same value as the reciprocal below (both IEEE-rounded), without an FP64 division
+        // per cell on GB300's narrow FP64 pipe; the FP32 forms keep the per-thread reciprocal,
+        // which measured faster there (register allocation of the 16-bit steps)
+        wnu = R(p.omega_nu);
     } else {
         wnu = rcp(R(p.tau0));
     }
@@ -797,9 +804,12 @@ __device__ __forceinline__ void collide(R (&m)[Lat<D>::Q], const R F[3], const P
                     }
                     if constexpr (FT::UNIT) {
                         // fma(0, ., fma(1, DM, hs)) of the general form: DM + s/2 rounded once (the
-                        // halving is exact), one packed instruction instead of a product and a sum
-                        if constexpr (sourced) m[t] = fma(R(0.5), s, DM);
-                        else m[t] = DM;
+                        // halving is exact). The standard collision writes it as one packed fma; the
+                        // general forms keep the product and the sum, which measured fewer spills
+                        // there (0-24 B against 16-44 B at 128 registers, FP32)
+                        if constexpr (!sourced) m[t] = DM;
+                        else if constexpr (FT::GEN) m[t] = DM + hs;
+                        else m[t] = fma(R(0.5), s, DM);
                     } else {
                         const R w = (ord(t) == 3) ? w3 : w4;
                         const R om = (ord(t) == 3) ? om3 : om4;

@@ -21,12 +21,19 @@ namespace cm {
 // as do the general forms (they spill twice as much at 5) and all FP32 steps (the forced FP32
 // LES loses 7 % at 5).
 #ifndef CM_PAIR_FX_BLOCKS
-#define CM_PAIR_FX_BLOCKS (CM_PAIR_MIN_BLOCKS + 1)
+#define CM_PAIR_FX_BLOCKS (CM_PAIR_MIN_BLOCKS + 2)
+#endif
+#ifndef CM_PAIR_FIELD_UNIT_BLOCKS
+#define CM_PAIR_FIELD_UNIT_BLOCKS (CM_PAIR_MIN_BLOCKS + 1)
+#endif
+#ifndef CM_PAIR_FIELD_DEV
+#define CM_PAIR_FIELD_DEV 0
 #endif
 template <class S, class FT>
 constexpr int pair_min_blocks() {
     if constexpr (sizeof(S) == 2) {
         if constexpr (FT::FX) return CM_PAIR_FX_BLOCKS;
+        if constexpr (FT::FIELD && FT::UNIT && !FT::GEN) return CM_PAIR_FIELD_UNIT_BLOCKS;
         return FT::SIMPLE ? CM_PAIR_MIN_BLOCKS + 2
                           : (!FT::GEN && (!FT::FIELD || FT::UNIT) ? CM_PAIR_MIN_BLOCKS + 1 : CM_PAIR_MIN_BLOCKS);
     }
@@ -46,7 +53,9 @@ template <class S, class FT> constexpr bool pair_adjacent() { return sizeof(S) =
 // Measured at 256^3: +1 % (Taylor-Green BF16/FP16) and +2.4 % (channel BF16) with the folded
 // weights, but -0.7 % with a force field (isotropic LES BF16) and -0.2 % for the unforced FP32
 // step; the FP32 steps and the force-field steps keep the explicit weights.
-template <class S, class FT> __host__ __device__ constexpr bool pair_dev() { return sizeof(S) == 2 && !FT::FIELD; }
+template <class S, class FT> __host__ __device__ constexpr bool pair_dev() {
+    return sizeof(S) == 2 && (!FT::FIELD || CM_PAIR_FIELD_DEV);
+}
 
 // Plane ring of the two-steps-per-pass schedule (launch_pair_two_steps): the intermediate state
 // t+1 lives in a small buffer of z-planes instead of a full state buffer. Plane z sits in slot

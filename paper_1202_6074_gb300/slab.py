@@ -117,20 +117,53 @@ class SlabRun:
     overlap = True steps engines that offer ``step_split`` (the library's cmlbm_step_split) in
     two parts: the boundary planes, whose faces the exchange then packs, on the engine's stream,
     and the interior planes on a stream of their own, so that the exchange of a step runs while
-    the interior of that step is computed. The results are the same bit for bit.
+    the interior of that step is computed. The results are the same bit for bit. The boundary
+    planes and the exchange then run on a CUDA stream of the highest priority (the library's
+    interior stream has the lowest), which the run creates: during step() the engines launch on
+    it, and at its end the caller's stream waits for it and the engines return to the caller's
+    stream.
     """
 
     def __init__(self, engines, exchange, overlap=False):
         self.engines = list(engines)
         self.exchange = exchange
         self.overlap = overlap
+        self.stream = None
+        self._split = [e for e in self.engines if hasattr(e, "step_split") and hasattr(e, "set_stream")]
+        if overlap and torch.cuda.is_available() and self._split:
+            _, highest = torch.cuda.Stream.priority_range()
+            self.stream = torch.cuda.Stream(device=self._split[0].device, priority=highest)
 
     def step(self, n=1):
+        if self.stream is None:
+            return self._step(n)
+        caller = torch.cuda.current_stream(self.stream.device)
+        self.stream.wait_stream(caller)
+        for e in self._split:
+            e.set_stream(self.stream)
+        try:
+            with torch.cuda.stream(self.stream):
+                self._step(n)
+        finally:
+            caller.wait_stream(self.stream)
+            for e in self._split:
+                e.set_stream(caller)
+
+    def _step(self, n):
         for _ in range(n):
-            for e in self.engines:
-                if self.overlap and hasattr(e, "step_split"):
-                    e.step_split()
-                else:
+            if self.overlap:
+                # every slab's boundary planes first, then the interiors: a kernel issued after a
+                # large one waits for the large one's blocks to be dispatched
+                for e in self.engines:
+                    if hasattr(e, "step_split"):
+                        e.step_split(1)
+                for e in self.engines:
+                    if hasattr(e, "step_split"):
+                        e.step_split(2)
+                    else:
+                        e.step(1)
+            else:
+                for e in self.engines:
                     e.step(1)
             self.exchange.exchange()
         if self.overlap:

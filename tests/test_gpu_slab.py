@@ -253,3 +253,30 @@ def test_split_step_equals_step_on_a_single_domain(cm, storage):
     a.close()
     b.close()
 
+
+
+def test_split_step_in_two_parts(cm):
+    """The boundary and interior parts issued in two calls give the plain step's state; the
+    parts must alternate, and a step or a state replacement between them is refused."""
+    c = dict(storage="f32", tau=0.6, omega_bulk=1.0, field=True)
+    rho, u, F = _fields(8)
+    a = _single(cm, c, rho, u, F)
+    b = _single(cm, c, rho, u, F)
+    for _ in range(3):
+        a.step_split(1)
+        a.step_split(2)
+    b.step(3)
+    assert torch.equal(a.get_state(), b.get_state())
+    with pytest.raises(cm.CmlbmError) as e:
+        a.step_split(2)                       # an interior part without its boundary part
+    assert e.value.code == cm.ERR_INVALID
+    a.step_split(1)
+    for bad in (lambda: a.step_split(1), lambda: a.step(1), lambda: a.set_state(b.get_state())):
+        with pytest.raises(cm.CmlbmError) as e:
+            bad()
+        assert e.value.code == cm.ERR_INVALID
+    a.step_split(2)
+    b.step(1)
+    assert torch.equal(a.get_state(), b.get_state())
+    a.close()
+    b.close()
