@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--flow", default="tgv", choices=["tgv", "hit"],
                     help="timed workload: the Taylor-Green vortex (headline) or the forced isotropic "
                          "turbulence LES (force field, Cs = 0.1) on the same n^3 box")
-    ap.add_argument("--only", default=None, choices=["channel", "hit"],
+    ap.add_argument("--only", default=None, choices=["channel", "hit", "tgv"],
                     help="run only this form (16-bit storage by --storage, shape by --shape) and print its "
                          "MLUPS; for profiling captures of one kernel variant")
     ap.add_argument("--shape", default=None, help="nx,ny,nz of the --only form")
@@ -701,11 +701,16 @@ def only_form(args):
         nx, ny, nz = (int(v) for v in (args.shape or "1024,256,256").split(","))
         ms, _ = run_channel(cm, st, args.form_steps, args.warmup, Dist0(), nx=nx, ny=ny, nz=nz)
         bpc = BYTES_PER_CELL[("D3Q27", st)]
-    else:
+    elif args.only == "hit":
         nx, ny, nz = (int(v) for v in (args.shape or "512,512,512").split(","))
         assert nx == ny == nz, "the forced isotropic turbulence form runs on a cube"
         ms, _ = run_hit_les(cm, nx, st, args.form_steps, args.warmup, Dist0())
         bpc = BYTES_PER_CELL[("D3Q27", st)] + 12
+    else:
+        nx, ny, nz = (int(v) for v in (args.shape or "256,256,256").split(","))
+        assert nx == ny == nz, "the Taylor-Green form runs on a cube"
+        ms, _, _, _, _ = run_tgv(cm, nx, st, args.form_steps, args.warmup, Dist0())
+        bpc = BYTES_PER_CELL[("D3Q27", st)]
     N = nx * ny * nz
     mlups = N * args.form_steps / (ms / 1e3) / 1e6
     print(json.dumps({"form": args.only, "shape": [nx, ny, nz], "storage": st, "steps": args.form_steps,
