@@ -13,9 +13,12 @@ constexpr int kBlock = 128;
 #ifndef CM_STEP_MIN_BLOCKS
 #define CM_STEP_MIN_BLOCKS 8
 #endif
-// grids up to this many cells launch the one-cell step with 32-thread blocks
+// grids up to this many cells launch the one-cell step with blocks of CM_SMALL_BLOCK threads
 #ifndef CM_SMALL_GRID
 #define CM_SMALL_GRID 65536
+#endif
+#ifndef CM_SMALL_BLOCK
+#define CM_SMALL_BLOCK 32
 #endif
 constexpr long long kSmallGrid = CM_SMALL_GRID;
 template <class S> constexpr int step_min_blocks() { return sizeof(typename Codec<S>::R) == 8 ? 1 : CM_STEP_MIN_BLOCKS; }
@@ -218,7 +221,7 @@ void launch_step_ft(const void* src, void* dst, const void* Ff, const Params& p,
     }
     // small grids: one warp per block so that the few blocks spread over as many SMs as possible
     // (the step is latency bound there; 128-thread blocks would leave most SMs idle)
-    const dim3 b = p.N <= kSmallGrid ? dim3(32, 1, 1) : cell_block(p.nx), g = cell_grid(p, b);
+    const dim3 b = p.N <= kSmallGrid ? dim3(CM_SMALL_BLOCK, 1, 1) : cell_block(p.nx), g = cell_grid(p, b);
     k_step<D, S, FT><<<g, b, 0, st>>>((const S*)src, (S*)dst, (const R*)Ff, typed<R>(p));
 }
 
