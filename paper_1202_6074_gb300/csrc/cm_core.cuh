@@ -161,14 +161,18 @@ template <class R> using scalar_t = typename Scalar<R>::T;
 // a channel): the source recursion keeps only its x terms, and the moments without an x
 // exponent get no source. The same values as UNIT (the terms left out are products with zero).
 // BIG: 64-bit element offsets (grids with Q * S >= 2^32).
+// FACT / RED: the factorized attractor (Sec. 13) / reduced compressibility (Sec. 12) fixed at
+// compile time instead of read from the parameters as GEN does (for SIMPLE collisions, the
+// unforced flows the two forms are most often run on).
 template <bool WALLS_, bool LES_, bool FIELD_, bool GEN_, bool SIMPLE_ = false, bool UNIT_ = false, bool BIG_ = false,
-          bool FX_ = false>
+          bool FX_ = false, bool FACT_ = false, bool RED_ = false>
 struct Feat {
     static constexpr bool WALLS = WALLS_, LES = LES_, FIELD = FIELD_, GEN = GEN_, SIMPLE = SIMPLE_, UNIT = UNIT_, BIG = BIG_,
-                          FX = FX_;
+                          FX = FX_, FACT = FACT_, RED = RED_;
     static_assert(!SIMPLE_ || (!FIELD_ && !GEN_), "SIMPLE excludes force fields and the general forms");
     static_assert(!UNIT_ || !SIMPLE_, "UNIT is a forced collision");
     static_assert(!FX_ || (UNIT_ && !FIELD_ && !GEN_), "FX is a UNIT collision with a uniform force along x");
+    static_assert(!(FACT_ || RED_) || (SIMPLE_ && !GEN_), "FACT / RED are SIMPLE collisions of one form");
 };
 
 // ------------------------------------------------------------------------------------------
@@ -507,7 +511,7 @@ template <int D, class R> __device__ __forceinline__ void raw_x_dev(R (&m)[Lat<D
 
 // rho - 1 and the momentum (Eqs. densitycalculation, velocitycalculation) from the raw x-line
 // moments: line l = (e_y + 1) + 3 (e_z + 1)
-template <int D, class R, bool GEN = true, bool FORCED = true, bool FYZ = true>
+template <int D, class R, bool GEN = true, bool FORCED = true, bool FYZ = true, bool RED = false>
 __device__ __forceinline__ Hydro<D, R> hydro_x(const R (&m)[Lat<D>::Q], const R F[3], const PR<scalar_t<R>>& p) {
     constexpr int NL = Lat<D>::Q / 3;
     Hydro<D, R> o;
@@ -534,7 +538,7 @@ __device__ __forceinline__ Hydro<D, R> hydro_x(const R (&m)[Lat<D>::Q], const R 
         o.jy = jy;
         o.jz = jz;
     }
-    const R inv = rcp((GEN && p.reduced) ? R(p.rho0) : R(1) + drho);
+    const R inv = rcp(RED || (GEN && p.reduced) ? R(p.rho0) : R(1) + drho);
     o.ux = o.jx * inv;
     o.uy = o.jy * inv;
     o.uz = (D == 3) ? o.jz * inv : R(0);
@@ -668,7 +672,7 @@ __device__ __forceinline__ void collide(R (&m)[Lat<D>::Q], const R F[3], const P
     constexpr int Q = Lat<D>::Q;
     if constexpr (DEV) raw_x_dev<D, R>(m);
     else raw_x<D, R>(m);
-    const Hydro<D, R> hy = hydro_x<D, R, FT::GEN, !FT::SIMPLE, !FT::FX>(m, F, p);
+    const Hydro<D, R> hy = hydro_x<D, R, FT::GEN, !FT::SIMPLE, !FT::FX, FT::RED>(m, F, p);
     const R drho = hy.drho, rho = R(1) + hy.drho, ndrho = -hy.drho;
     const R u[3] = {hy.ux, hy.uy, hy.uz};
     central_forward_from_x<D, R>(m, u[0], u[1], u[2]);
@@ -742,7 +746,32 @@ __device__ __forceinline__ void collide(R (&m)[Lat<D>::Q], const R F[3], const P
     const R Tyz = omn * Pyz;
     const R w3 = R(p.omega3), w4 = R(p.omega4);
     const R om3 = R(T(1) - p.omega3), om4 = R(T(1) - p.omega4);
-    const bool factorized = FT::GEN && p.attractor != 0;
+    const bool factorized = (FT::GEN && p.attractor != 0) || FT::FACT;
+
+    // the factorized attractor of moment (a, b, c) (Sec. 13: products of the relaxed second-order
+    // moments over rho^(k-1)) as a deviation from the weights' moment, where the pattern has a
+    // product rule; DM (the Maxwellian one) otherwise
+    auto factorized_dm = [&](auto AI, auto BI, auto CI, R DM) -> R {
+        constexpr int a = decltype(AI)::value, b = decltype(BI)::value, c = decltype(CI)::value;
+        constexpr int ones = (a == 1) + (b == 1) + (c == 1);
+        constexpr int twos = (a == 2) + (b == 2) + (c == 2);
+        if constexpr (ones == 0) {
+            const R pt[3] = {Txx * irho, Tyy * irho, Tzz * irho};
+            R prodp = R(1);
+            if constexpr (a == 2) prodp = prodp * (third + pt[0]);
+            if constexpr (b == 2) prodp = prodp * (third + pt[1]);
+            if constexpr (c == 2) prodp = prodp * (third + pt[2]);
+            return fma(drho, prodp, excess<R, a == 2, b == 2, c == 2>(pt) - excess<R, a == 2, b == 2, c == 2>(q));
+        } else if constexpr (ones == 2 && twos == 1) {
+            constexpr int dtwo = (a == 2) ? 0 : (b == 2) ? 1 : 2;
+            const R Tdg = dtwo == 0 ? Txx : dtwo == 1 ? Tyy : Tzz;
+            const R Toff = (a != 1) ? Tyz : (b != 1) ? Txz : Txy;
+            const R uoff = (a != 1) ? u[1] * u[2] : (b != 1) ? u[0] * u[2] : u[0] * u[1];
+            return fma(Toff, fma(Tdg, irho, third), -((third + q[dtwo]) * uoff));
+        } else {
+            return DM;
+        }
+    };
 
     if constexpr (FT::SIMPLE) {
         // no source and omega_3 = omega_4 = 1: orders >= 3 are set to their attractors
@@ -751,12 +780,17 @@ __device__ __forceinline__ void collide(R (&m)[Lat<D>::Q], const R F[3], const P
             if constexpr (ord(t) >= 3) {
                 constexpr int a = ex_a(t), b = ex_b(t), c = ex_c(t);
                 constexpr bool even = (a % 2 == 0) && (b % 2 == 0) && (c % 2 == 0);
+                R DM;
                 if constexpr (even) {
                     const R tp = R((T)third_pow((a == 2) + (b == 2) + (c == 2)));
-                    m[t] = fma(drho, tp, -excess<R, a == 2, b == 2, c == 2>(q));
+                    DM = fma(drho, tp, -excess<R, a == 2, b == 2, c == 2>(q));
                 } else {
-                    m[t] = -weight_cm<R, a, b, c>(cw);
+                    DM = -weight_cm<R, a, b, c>(cw);
                 }
+                if constexpr (FT::FACT)
+                    DM = factorized_dm(std::integral_constant<int, a>{}, std::integral_constant<int, b>{},
+                                       std::integral_constant<int, c>{}, DM);
+                m[t] = DM;
             }
         });
     } else {
@@ -784,24 +818,9 @@ __device__ __forceinline__ void collide(R (&m)[Lat<D>::Q], const R F[3], const P
                     R DM;
                     if constexpr (even) DM = fma(drho, tp, -excess<R, a == 2, b == 2, c == 2>(q));
                     else DM = -kw;
-                    if (factorized) {
-                        // Sec. 13: products of relaxed second-order moments / rho^(k-1)
-                        constexpr int ones = (a == 1) + (b == 1) + (c == 1);
-                        if constexpr (ones == 0) {
-                            const R pt[3] = {Txx * irho, Tyy * irho, Tzz * irho};
-                            R prodp = R(1);
-                            if constexpr (a == 2) prodp = prodp * (third + pt[0]);
-                            if constexpr (b == 2) prodp = prodp * (third + pt[1]);
-                            if constexpr (c == 2) prodp = prodp * (third + pt[2]);
-                            DM = fma(drho, prodp, excess<R, a == 2, b == 2, c == 2>(pt) - excess<R, a == 2, b == 2, c == 2>(q));
-                        } else if constexpr (ones == 2 && twos == 1) {
-                            constexpr int dtwo = (a == 2) ? 0 : (b == 2) ? 1 : 2;
-                            const R Tdg = dtwo == 0 ? Txx : dtwo == 1 ? Tyy : Tzz;
-                            const R Toff = (a != 1) ? Tyz : (b != 1) ? Txz : Txy;
-                            const R uoff = (a != 1) ? u[1] * u[2] : (b != 1) ? u[0] * u[2] : u[0] * u[1];
-                            DM = fma(Toff, fma(Tdg, irho, third), -((third + q[dtwo]) * uoff));
-                        }
-                    }
+                    if (factorized)
+                        DM = factorized_dm(std::integral_constant<int, a>{}, std::integral_constant<int, b>{},
+                                           std::integral_constant<int, c>{}, DM);
                     if constexpr (FT::UNIT) {
                         // fma(0, ., fma(1, DM, hs)) of the general form: DM + s/2 rounded once (the
                         // halving is exact). The standard collision writes it as one packed fma; the

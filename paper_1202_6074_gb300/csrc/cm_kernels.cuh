@@ -236,6 +236,17 @@ void launch_step_g(const void* src, void* dst, const void* Ff, const Params& p, 
     if (p.attractor != 0 || p.reduced) {
         if constexpr (D == 3 && sizeof(R) == 4) {
             if (p.pair && p.omega3 == 1.0 && p.omega4 == 1.0) {
+                if constexpr (!F) {
+                    // one of the two forms, unforced: its SIMPLE collision with the form fixed at
+                    // compile time
+                    if (simple_collision(p) && (p.attractor != 0) != (p.reduced != 0)) {
+                        if (p.attractor != 0)
+                            launch_pair<S, Feat<W, L, false, false, true, false, false, false, true, false>>(src, dst, Ff, p, st);
+                        else
+                            launch_pair<S, Feat<W, L, false, false, true, false, false, false, false, true>>(src, dst, Ff, p, st);
+                        return;
+                    }
+                }
                 launch_step_ft<D, S, Feat<W, L, F, true, false, true>>(src, dst, Ff, p, st);
                 return;
             }

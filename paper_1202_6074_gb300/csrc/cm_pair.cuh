@@ -433,6 +433,18 @@ int launch_pair_two_steps(const void* A, void* C, void* ring, int P, int slots, 
     template void launch_pair<S, Feat<true, true, false, true, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);   \
     template void launch_pair<S, Feat<true, true, true, true, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);
 
+// the unforced SIMPLE collision with the factorized attractor or reduced compressibility fixed at
+// compile time
+#define CM_PAIR_INSTANTIATE_FORMS(S)                                                                         \
+    template void launch_pair<S, Feat<false, false, false, false, true, false, false, false, true, false>>(const void*, void*, const void*, const Params&, cudaStream_t); \
+    template void launch_pair<S, Feat<false, true, false, false, true, false, false, false, true, false>>(const void*, void*, const void*, const Params&, cudaStream_t);  \
+    template void launch_pair<S, Feat<true, false, false, false, true, false, false, false, true, false>>(const void*, void*, const void*, const Params&, cudaStream_t);  \
+    template void launch_pair<S, Feat<true, true, false, false, true, false, false, false, true, false>>(const void*, void*, const void*, const Params&, cudaStream_t);   \
+    template void launch_pair<S, Feat<false, false, false, false, true, false, false, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t); \
+    template void launch_pair<S, Feat<false, true, false, false, true, false, false, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);  \
+    template void launch_pair<S, Feat<true, false, false, false, true, false, false, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);  \
+    template void launch_pair<S, Feat<true, true, false, false, true, false, false, false, false, true>>(const void*, void*, const void*, const Params&, cudaStream_t);
+
 // the general forms (factorized attractor, reduced compressibility), in translation units of
 // their own so that the library builds in parallel
 #define CM_PAIR_INSTANTIATE_GEN(S)                                                                          \

@@ -447,6 +447,12 @@ PAIR_CASES = {
                                                      [[0.01, 0, 0], [0, 0.02, 0]]])),
     "pair_bulk_follows_shear_les": dict(lattice="D3Q27", shape=(4, 6, 192), flow="tgv",
                                         kw=dict(tau=0.51, smagorinsky_cs=0.12, omega_3=1.3, omega_4=0.9)),
+    # unforced, unit higher-order rates: the SIMPLE collision with the form fixed at compile time
+    "pair_factorized_unforced": dict(lattice="D3Q27", shape=(5, 6, 64), flow="tgv_unforced",
+                                     kw=dict(tau=0.57, attractor="factorized", omega_bulk=1.1)),
+    "pair_reduced_unforced_walls_les": dict(lattice="D3Q27", shape=(5, 8, 128), flow="tgv_unforced",
+                                            kw=dict(tau=0.6, reduced_compressibility=True, rho0=1.02,
+                                                    smagorinsky_cs=0.1, bc=("periodic", "bounceback", "periodic"))),
 }
 
 
