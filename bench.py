@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--flow", default="tgv", choices=["tgv", "hit"],
                     help="timed workload: the Taylor-Green vortex (headline) or the forced isotropic "
                          "turbulence LES (force field, Cs = 0.1) on the same n^3 box")
-    ap.add_argument("--only", default=None, choices=["channel", "hit", "tgv"],
+    ap.add_argument("--only", default=None, choices=["channel", "hit", "tgv", "adjoint"],
                     help="run only this form (16-bit storage by --storage, shape by --shape) and print its "
                          "MLUPS; for profiling captures of one kernel variant")
     ap.add_argument("--shape", default=None, help="nx,ny,nz of the --only form")
@@ -697,6 +697,13 @@ def only_form(args):
     from paper_1202_6074_gb300 import cmlbm as cm
 
     st = "bf16" if args.storage == "f32" and args.only == "channel" else args.storage
+    if args.only == "adjoint":
+        from paper_1202_6074_gb300 import rollout
+
+        n = int((args.shape or "128").split(",")[0])
+        out = rollout.benchmark(cm, n=n, steps=args.form_steps, segment=50)
+        print(json.dumps({"form": "adjoint", "shape": [n, n, n], "storage": "f32", **out}))
+        return
     if args.only == "channel":
         nx, ny, nz = (int(v) for v in (args.shape or "1024,256,256").split(","))
         ms, _ = run_channel(cm, st, args.form_steps, args.warmup, Dist0(), nx=nx, ny=ny, nz=nz)

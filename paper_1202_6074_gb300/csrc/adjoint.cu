@@ -109,6 +109,58 @@ __device__ __forceinline__ void pull_source(int i, int x, int y, int z, const PR
     }
 }
 
+// The transpose of the pull (a scatter to the entries the pull of cell (x, y, z) reads): direction
+// i of the vector v goes to entry (i, x - e_i) with the periodic wrap, or to (opp(i), x) where the
+// link crosses a wall. The per-axis source coordinates and the nine row offsets are computed once,
+// as the pull computes them, instead of per direction.
+template <int D, bool WALLS, class R>
+__device__ __forceinline__ void scatter_pull_T(R* __restrict__ out, int x, int y, int z, const PR<R>& p,
+                                               const R (&v)[Lat<D>::Q]) {
+    const unsigned N = p.N;
+    int xs[3], ys[3], zs[3];
+    bool xo[3] = {false, false, false}, yo[3] = {false, false, false}, zo[3] = {false, false, false};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {          // slot k <-> e = k - 1, source coordinate = x - e
+        int sx = x + 1 - k, sy = y + 1 - k, sz = z + 1 - k;
+        if (sx < 0 || sx >= p.nx) {
+            if (!WALLS || p.bc[0] != 1) sx += (sx < 0) ? p.nx : -p.nx;
+            else xo[k] = true;
+        }
+        if (sy < 0 || sy >= p.ny) {
+            if (!WALLS || p.bc[1] != 1) sy += (sy < 0) ? p.ny : -p.ny;
+            else yo[k] = true;
+        }
+        if constexpr (D == 3) {
+            if (sz < 0 || sz >= p.nz) {
+                if (!WALLS || p.bc[2] != 1) sz += (sz < 0) ? p.nz : -p.nz;
+                else zo[k] = true;
+            }
+        } else {
+            sz = 0;
+        }
+        xs[k] = sx;
+        ys[k] = sy;
+        zs[k] = sz;
+    }
+    const unsigned cell = (unsigned)((z * p.ny + y) * p.nx + x);
+    unsigned row[3][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) row[c][b] = (unsigned)((zs[c] * p.ny + ys[b]) * p.nx);
+    sfor<Lat<D>::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int a = Lat<D>::ex(i) + 1, b = Lat<D>::ey(i) + 1, c = Lat<D>::ez(i) + 1;
+        const unsigned pulled = i * N + row[c][b] + (unsigned)xs[a];
+        if constexpr (WALLS) {
+            const bool bounced = xo[a] || yo[b] || zo[c];
+            out[bounced ? Lat<D>::opp(i) * N + cell : pulled] = v[slot<D>(i)];
+        } else {
+            out[pulled] = v[slot<D>(i)];
+        }
+    });
+}
+
 template <int D, class S, bool WALLS>
 __global__ void __launch_bounds__(kBlock) k_adjoint_terminal(const S* __restrict__ state, const typename Codec<S>::R* __restrict__ Ff,
                                                             PR<typename Codec<S>::R> p, const double* __restrict__ dLdu,
@@ -391,13 +443,7 @@ __global__ void __launch_bounds__(kBlock, CM_ADJ_MIN_BLOCKS) k_adjoint_step(cons
     Fb[2] += R(0.5) * irho * ub[2];
 
     // scatter through the transpose of the pull
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        int dir;
-        unsigned sc;
-        pull_source<D, WALLS, R>(i, x, y, z, p, dir, sc);
-        lam_out[(unsigned)dir * p.N + sc] = L[slot<D>(i)];
-    }
+    scatter_pull_T<D, WALLS, R>(lam_out, x, y, z, p, L);
 #pragma unroll
     for (int d = 0; d < D; ++d) {
         if constexpr (ACC == kAccF64) {
