@@ -40,6 +40,7 @@ FALLBACK_HBM = 6800.0
 OMEGA_BULK = 1.0
 HIT_TAU = 0.5005       # base relaxation time of the forced isotropic turbulence LES
 FILTERED_BYTES_PER_CELL = 136 + 36 + 40 + 228
+ADJOINT_SEGMENT_BYTES_PER_CELL = 3 * 108 + 12 + 24
 
 
 def parse():
@@ -674,6 +675,12 @@ def our_arm(args, dist):
         if "forward_MLUPS" in adj:
             adj["backward_vs_forward"] = adj["backward_MLUPS"] / adj["forward_MLUPS"]
             adj["fwd_plus_adjoint_vs_forward"] = adj["fwd_plus_adjoint_MLUPS"] / adj["forward_MLUPS"]
+        if "adjoint_step_us" in adj:
+            # a step inside a checkpoint segment: state, lambda in and out (27 x 4 B each), the
+            # force field (12 B) and the FP32 segment accumulator read and written (24 B)
+            adj["adjoint_step_bytes_per_cell"] = ADJOINT_SEGMENT_BYTES_PER_CELL
+            adj["adjoint_step_frac_of_hbm"] = (adj["adjoint_step_MLUPS"] * ADJOINT_SEGMENT_BYTES_PER_CELL / 1e3
+                                               / peaks()[0]["hbm_gbs"])
         line["forms"] = forms
         if not args.no_cpu:
             line["cpu_baseline"] = cpu_baseline()
@@ -702,6 +709,8 @@ def only_form(args):
 
         n = int((args.shape or "128").split(",")[0])
         out = rollout.benchmark(cm, n=n, steps=args.form_steps, segment=50)
+        out["adjoint_step_frac_of_hbm"] = (out["adjoint_step_MLUPS"] * ADJOINT_SEGMENT_BYTES_PER_CELL / 1e3
+                                           / peaks()[0]["hbm_gbs"])
         print(json.dumps({"form": "adjoint", "shape": [n, n, n], "storage": "f32", **out}))
         return
     if args.only == "channel":

@@ -111,6 +111,18 @@ template <bool BIG, class P> __host__ __device__ __forceinline__ Ix<BIG> cell_co
 
 // reciprocal: IEEE-rounded intrinsic in FP32, plain division in FP64
 __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+// the PTX approximations (sqrt.approx.f32, rcp.approx.f32: a single instruction each, within
+// a few ulp of the rounded result), used where the eddy viscosity is evaluated (collide)
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 
 // Two cells in one value: the packed FP32 instructions of sm_100 and later (FADD2, FMUL2,
@@ -142,6 +154,15 @@ __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
 __device__ __forceinline__ F2 fma(F2 a, F2 b, F2 c) { return f2(__ffma2_rn(a.v, b.v, c.v)); }
 __device__ __forceinline__ F2 rcp(F2 x) { return F2(__frcp_rn(x.v.x), __frcp_rn(x.v.y)); }
 __device__ __forceinline__ F2 sqrt(F2 x) { return F2(sqrtf(x.v.x), sqrtf(x.v.y)); }
+// square root and reciprocal of the eddy-viscosity relaxation time: the approximations in FP32
+// (measured +4 % on the 16-bit wall-bounded LES step, which is bound by its FP32 arithmetic),
+// the rounded operations in FP64
+__device__ __forceinline__ float les_sqrt(float x) { return sqrt_approx(x); }
+__device__ __forceinline__ float les_rcp(float x) { return rcp_approx(x); }
+__device__ __forceinline__ double les_sqrt(double x) { return ::sqrt(x); }
+__device__ __forceinline__ double les_rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ F2 les_sqrt(F2 x) { return F2(sqrt_approx(x.v.x), sqrt_approx(x.v.y)); }
+__device__ __forceinline__ F2 les_rcp(F2 x) { return F2(rcp_approx(x.v.x), rcp_approx(x.v.y)); }
 
 // scalar type of the parameters (and of per-row quantities) for an arithmetic type
 template <class R> struct Scalar { using T = R; };
@@ -336,16 +357,17 @@ template <class R> __device__ __forceinline__ void fwd1(R& a, R& b, R& c, R nu, 
     b = fma(nu, m0, s1);
     c = fma(u2, m0, fma(ntu, s1, s2));
 }
-// inverse: (m0, m1, m2) -> (f-, f0, f+); f+- = (r2 +- r1) / 2, f0 = m0 - r2 with the raw
-// moments r1 = sum f e, r2 = sum f e^2 (halving is exact, so each output is rounded once)
-template <class R> __device__ __forceinline__ void inv1(R& a, R& b, R& c, R u, R tu, R u2) {
+// inverse: (m0, m1, m2) -> (2 f-, f0, 2 f+) with the raw moments r1 = sum f e, r2 = sum f e^2:
+// f+- = (r2 +- r1) / 2 and f0 = m0 - r2. The halving is left out: the outputs for e = -+1 come
+// out doubled, exactly (a power of two commutes with rounding), and the sweeps that follow are
+// linear, so the factor travels with them to the last sweep, whose per-line constants absorb it.
+template <class R> __device__ __forceinline__ void inv1x2(R& a, R& b, R& c, R u, R tu, R u2) {
     const R m0 = a, m1 = b, m2 = c;
     const R r1 = fma(u, m0, m1);
     const R r2 = fma(u2, m0, fma(tu, m1, m2));
-    const R h2 = R(0.5) * r2;
-    a = fma(R(-0.5), r1, h2);
-    b = fma(R(-1), r2, m0);
-    c = fma(R(0.5), r1, h2);
+    a = r2 - r1;
+    b = m0 - r2;
+    c = r2 + r1;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -587,49 +609,60 @@ __device__ __forceinline__ void central_forward_from_x(R (&m)[Lat<D>::Q], R ux, 
     }
 }
 
-// Inverse sweeps: central moments about u -> populations (slot order).
+// Inverse sweeps: central moments about u -> populations (slot order). Every sweep leaves out
+// the halving of f-+ = (r2 -+ r1) / 2 (inv1x2), so that the x-line l = (e_y + 1) + 3 (e_z + 1)
+// arrives scaled by 2^k, k = |e_y| + |e_z|. What the last (x) sweep returns, by OUT:
+//   kInvPlain:  the populations h (its constants carry 1/2 and 2^-k);
+//   kInvDev:    the deviations d = h / w (the inverse weights folded into those constants);
+//   kInvScaled: 2^n h with n = |e_x| + |e_y| + |e_z| (no constants at all), for a caller that
+//               multiplies every population by a constant anyway (inv_weight_scaled below).
+// Each is bitwise the result of halving in every sweep (a power of two commutes with rounding).
+enum { kInvPlain = 0, kInvDev = 1, kInvScaled = 2 };
+template <int D, class R, int OUT>
+__device__ __forceinline__ void central_inverse_impl(R (&m)[Lat<D>::Q], R ux, R uy, R uz) {
+    using T = scalar_t<R>;
+    constexpr int NL = Lat<D>::Q / 3;
+    const R tx = ux + ux, ty = uy + uy, tz = uz + uz, qx = ux * ux, qy = uy * uy, qz = uz * uz;
+    if constexpr (D == 3) {
+#pragma unroll
+        for (int t = 0; t < 9; ++t) inv1x2(m[t], m[9 + t], m[18 + t], uz, tz, qz);
+    }
+#pragma unroll
+    for (int c = 0; c < Lat<D>::NZ; ++c)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) inv1x2(m[9 * c + a], m[9 * c + 3 + a], m[9 * c + 6 + a], uy, ty, qy);
+    if constexpr (OUT == kInvScaled) {
+#pragma unroll
+        for (int l = 0; l < NL; ++l) inv1x2(m[3 * l], m[3 * l + 1], m[3 * l + 2], ux, tx, qx);
+    } else {
+        sfor<NL>([&](auto LI) {
+            constexpr int l = decltype(LI)::value;
+            constexpr int k = (l % 3 != 1) + (l / 3 != 1 && D == 3);
+            constexpr double sk = k == 0 ? 1.0 : k == 1 ? 0.5 : 0.25;
+            constexpr bool dev = OUT == kInvDev;
+            constexpr T he = (T)((dev ? 0.5 / weight_slot<D>(3 * l) : 0.5) * sk),
+                        i0 = (T)((dev ? 1.0 / weight_slot<D>(3 * l + 1) : 1.0) * sk);
+            const R m0 = m[3 * l], m1 = m[3 * l + 1], m2 = m[3 * l + 2];
+            const R r1 = fma(ux, m0, m1);
+            const R r2 = fma(qx, m0, fma(tx, m1, m2));
+            const R hr2 = r2 * R(he);
+            m[3 * l] = fma(R(-he), r1, hr2);
+            if constexpr (i0 == T(1)) m[3 * l + 1] = m0 - r2;
+            else m[3 * l + 1] = (m0 - r2) * R(i0);
+            m[3 * l + 2] = fma(R(he), r1, hr2);
+        });
+    }
+}
 template <int D, class R>
 __device__ __forceinline__ void central_inverse(R (&m)[Lat<D>::Q], R ux, R uy, R uz) {
-    constexpr int NL = Lat<D>::Q / 3;
-    const R tx = ux + ux, ty = uy + uy, tz = uz + uz, qx = ux * ux, qy = uy * uy, qz = uz * uz;
-    if constexpr (D == 3) {
-#pragma unroll
-        for (int t = 0; t < 9; ++t) inv1(m[t], m[9 + t], m[18 + t], uz, tz, qz);
-    }
-#pragma unroll
-    for (int c = 0; c < Lat<D>::NZ; ++c)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) inv1(m[9 * c + a], m[9 * c + 3 + a], m[9 * c + 6 + a], uy, ty, qy);
-#pragma unroll
-    for (int l = 0; l < NL; ++l) inv1(m[3 * l], m[3 * l + 1], m[3 * l + 2], ux, tx, qx);
+    central_inverse_impl<D, R, kInvPlain>(m, ux, uy, uz);
 }
 
-// central_inverse() with the populations' inverse weights folded into its last (x) sweep, so that
-// it returns the deviations d = h / w: on a line d_-+ = (r2 -+ r1) / (2 w_e), d_0 = (m0 - r2) / w_0.
-template <int D, class R>
-__device__ __forceinline__ void central_inverse_dev(R (&m)[Lat<D>::Q], R ux, R uy, R uz) {
-    constexpr int NL = Lat<D>::Q / 3;
-    const R tx = ux + ux, ty = uy + uy, tz = uz + uz, qx = ux * ux, qy = uy * uy, qz = uz * uz;
-    if constexpr (D == 3) {
-#pragma unroll
-        for (int t = 0; t < 9; ++t) inv1(m[t], m[9 + t], m[18 + t], uz, tz, qz);
-    }
-#pragma unroll
-    for (int c = 0; c < Lat<D>::NZ; ++c)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) inv1(m[9 * c + a], m[9 * c + 3 + a], m[9 * c + 6 + a], uy, ty, qy);
-    sfor<NL>([&](auto LI) {
-        constexpr int l = decltype(LI)::value;
-        constexpr scalar_t<R> he = (scalar_t<R>)(0.5 / weight_slot<D>(3 * l)),
-                               i0 = (scalar_t<R>)(1.0 / weight_slot<D>(3 * l + 1));
-        const R m0 = m[3 * l], m1 = m[3 * l + 1], m2 = m[3 * l + 2];
-        const R r1 = fma(ux, m0, m1);
-        const R r2 = fma(qx, m0, fma(tx, m1, m2));
-        const R hr2 = r2 * R(he);
-        m[3 * l] = fma(R(-he), r1, hr2);
-        m[3 * l + 1] = (m0 - r2) * R(i0);
-        m[3 * l + 2] = fma(R(he), r1, hr2);
-    });
+// The constant that turns the collision's output for direction i (2^n h, see collide) into the
+// stored deviation d = h / w: 1 / (2^n w_i), n = |e_x| + |e_y| + |e_z|.
+template <int D> __host__ __device__ constexpr double inv_weight_scaled(int i) {
+    const int n = (Lat<D>::ex(i) != 0) + (Lat<D>::ey(i) != 0) + (D == 3 && Lat<D>::ez(i) != 0);
+    return inv_weight<D>(i) / double(1 << n);
 }
 
 // prod_{d in S}(1/3 + q_d) - 3^{-|S|} without cancellation (all terms are non-negative):
@@ -661,8 +694,10 @@ template <class R, int a, int b, int c> __device__ __forceinline__ R weight_cm(c
 // ------------------------------------------------------------------------------------------
 // The collision in central-moment space (generic form; see the file header and cmlbm.h).
 // In: h deviation populations (slot order), force F, the eddy-viscosity constant cs_eff (0 = off).
-// Out: h holds the post-collision deviation populations. With DEV the populations come in and
-// go out as the stored deviations d = h / w (the weights folded into the first and last sweeps).
+// Out: h holds the post-collision deviation populations h, each scaled by 2^n (n = |e_x| + |e_y|
+// + |e_z| of its direction, see central_inverse_impl): the caller stores h * inv_weight_scaled.
+// With DEV the populations come in and go out as the stored deviations d = h / w (the weights
+// folded into the first and last sweeps).
 // R is the arithmetic type (double, float, or F2 for two cells of one row; cs_eff and the
 // parameters are then scalars shared by both cells).
 // ------------------------------------------------------------------------------------------
@@ -707,12 +742,12 @@ __device__ __forceinline__ void collide(R (&m)[Lat<D>::Q], const R F[3], const P
             R O2 = Pxy * Pxy;
             O2 = fma(Pxz, Pxz, O2);
             O2 = fma(Pyz, Pyz, O2);
-            const R Qn = sqrt(fma(R(2), O2, Q2));
+            const R Qn = les_sqrt(fma(R(2), O2, Q2));
             // tau_eff = (tau + sqrt(tau^2 + 18 sqrt(2) C^2 |Pi| / rho)) / 2
             const R k = R(T(25.455844122715710878) * cs_eff * cs_eff);
-            tau = R(0.5) * (tau + sqrt(fma(tau, tau, k * Qn * irho)));
+            tau = R(0.5) * (tau + les_sqrt(fma(tau, tau, k * Qn * irho)));
         }
-        wnu = rcp(tau);
+        wnu = les_rcp(tau);
     } else if constexpr (std::is_same_v<R, double>) {
         // the same value as the reciprocal below (both IEEE-rounded), without an FP64 division
         // per cell on GB300's narrow FP64 pipe; the FP32 forms keep the per-thread reciprocal,
@@ -860,8 +895,7 @@ __device__ __forceinline__ void collide(R (&m)[Lat<D>::Q], const R F[3], const P
     }
     // zeroth order unchanged (m[0] = drho)
 
-    if constexpr (DEV) central_inverse_dev<D, R>(m, u[0], u[1], u[2]);
-    else central_inverse<D, R>(m, u[0], u[1], u[2]);
+    central_inverse_impl<D, R, DEV ? kInvDev : kInvScaled>(m, u[0], u[1], u[2]);
 }
 
 // Equilibrium deviations fbar - w for (rho, u, F): central moments kappa^M - sigma^M / 2 about u

@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S>()) k_step(const S* 
     collide<D, R, FT>(h, F, p, smagorinsky_constant<R, FT::LES>(p, y));
     sfor<Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        constexpr R iw = (R)inv_weight<D>(i);
+        constexpr R iw = (R)inv_weight_scaled<D>(i);
         Codec<S>::st(dst + (IX(i) * PS + cell), h[slot<D>(i)] * iw);
     });
 }

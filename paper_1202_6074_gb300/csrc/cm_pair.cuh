@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(kBlock, pair_min_blocks<S, FT>()) k_step_pair(
     collide<3, F2, FT, DEV>(h, F, p, smagorinsky_constant<float, FT::LES>(p, y));
     sfor<27>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        const F2 v = DEV ? h[slot<3>(i)] : h[slot<3>(i)] * F2((float)inv_weight<3>(i));
+        const F2 v = DEV ? h[slot<3>(i)] : h[slot<3>(i)] * F2((float)inv_weight_scaled<3>(i));
         if constexpr (ADJ) {
             Codec<S>::st2(dst + dA + (size_t)PS * i, v.v.x, v.v.y);
         } else if constexpr (sizeof(S) == 2) {

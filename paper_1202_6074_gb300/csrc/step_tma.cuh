@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(TX + 32, 2) k_step_tma(const __grid_constant__
         collide<3, R, FT>(h, F, p, smagorinsky_constant<R, FT::LES>(p, y));
         sfor<Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
-            constexpr R iw = (R)inv_weight<3>(i);
+            constexpr R iw = (R)inv_weight_scaled<3>(i);
             Codec<S>::st(dst + (i * N + cell), h[slot<3>(i)] * iw);
         });
     }

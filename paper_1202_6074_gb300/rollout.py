@@ -126,6 +126,25 @@ def benchmark(cm, n=128, steps=100, segment=50):
     out = {"forward_MLUPS": N * steps / (t1 - t0) / 1e6, "backward_MLUPS": N * steps / (t2 - t1) / 1e6,
            "fwd_plus_adjoint_MLUPS": N * steps / (t2 - t0) / 1e6, "steps": steps, "segment": segment,
            "launches": s.launch_count - l0, "grad_norm": float(Fp.grad.norm())}
+    # the adjoint step alone (CUDA events on the handle's stream, which is the current stream):
+    # a step inside a segment (FP32 accumulator) and a folding step (FP32 into FP64)
+    lam = torch.zeros((s.Q,) + s.shape, dtype=torch.float32, device="cuda")
+    lam2 = torch.empty_like(lam)
+    seg = torch.zeros((3,) + s.shape, dtype=torch.float32, device="cuda")
+    dLdF = torch.zeros((3,) + s.shape, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    for fold, key in ((False, "adjoint_step_us"), (True, "adjoint_fold_step_us")):
+        for _ in range(3):
+            s.step_adjoint_segment(s0, lam, lam2, seg, dLdF, fold)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 20
+        e0.record(stream)
+        for _ in range(reps):
+            s.step_adjoint_segment(s0, lam, lam2, seg, dLdF, fold)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[key] = e0.elapsed_time(e1) * 1e3 / reps
+    out["adjoint_step_MLUPS"] = N / out["adjoint_step_us"]
     s.close()
     return out
 
