@@ -357,6 +357,16 @@ template <class R> __device__ __forceinline__ void fwd1(R& a, R& b, R& c, R nu, 
     b = fma(nu, m0, s1);
     c = fma(u2, m0, fma(ntu, s1, s2));
 }
+// the same on populations weighted by the relative 1D weights (1, 4, 1) of e = (-1, 0, +1):
+// m_k = sum r1(e) f (e - u)^k, the sum a multiply-add by 4 in place of an add
+template <class R> __device__ __forceinline__ void fwd1r(R& a, R& b, R& c, R nu, R ntu, R u2) {
+    const R s1 = c - a;
+    const R s2 = c + a;
+    const R m0 = fma(R(4), b, s2);
+    a = m0;
+    b = fma(nu, m0, s1);
+    c = fma(u2, m0, fma(ntu, s1, s2));
+}
 // inverse: (m0, m1, m2) -> (2 f-, f0, 2 f+) with the raw moments r1 = sum f e, r2 = sum f e^2:
 // f+- = (r2 +- r1) / 2 and f0 = m0 - r2. The halving is left out: the outputs for e = -+1 come
 // out doubled, exactly (a power of two commutes with rounding), and the sweeps that follow are
@@ -371,9 +381,10 @@ template <class R> __device__ __forceinline__ void inv1x2(R& a, R& b, R& c, R u,
 }
 
 // ------------------------------------------------------------------------------------------
-// Pull with periodic wrap and half-way bounce-back; fills h (deviation populations, slot order)
+// Pull with periodic wrap and half-way bounce-back; fills h (slot order) with the deviation
+// populations h = w d, or with WEIGHTED = false the stored deviations d themselves
 // ------------------------------------------------------------------------------------------
-template <int D, class S, bool WALLS, bool BIG = false>
+template <int D, class S, bool WALLS, bool BIG = false, bool WEIGHTED = true>
 __device__ __forceinline__ void gather_impl(const S* __restrict__ src, int x, int y, int z, const PR<typename Codec<S>::R>& p,
                                        typename Codec<S>::R (&h)[Lat<D>::Q]) {
     using R = typename Codec<S>::R;
@@ -433,9 +444,10 @@ __device__ __forceinline__ void gather_impl(const S* __restrict__ src, int x, in
             const int cnt = (int)bx + (int)by + (int)bz;
             const R inv_cnt = cnt >= 3 ? R(1) / 3 : cnt == 2 ? R(0.5) : R(1);
             d += R(6) * eu * inv_cnt;
-            h[slot<D>(i)] = d * w;
+            h[slot<D>(i)] = WEIGHTED ? d * w : d;
         } else {
-            h[slot<D>(i)] = Codec<S>::ld(src + (IX(i) * PS + row[c][b] + (unsigned)xs[a])) * w;
+            const R d = Codec<S>::ld(src + (IX(i) * PS + row[c][b] + (unsigned)xs[a]));
+            h[slot<D>(i)] = WEIGHTED ? d * w : d;
         }
     });
 }
@@ -444,16 +456,16 @@ __device__ __forceinline__ void gather_impl(const S* __restrict__ src, int x, in
 // or last layer of a bounce-back axis); everywhere else the periodic pull, which never leaves the
 // box on a wall axis there. With x-rows per warp, y and z are warp-uniform, so the branch only
 // diverges on x walls.
-template <int D, class S, bool WALLS, bool BIG = false>
+template <int D, class S, bool WALLS, bool BIG = false, bool WEIGHTED = true>
 __device__ __forceinline__ void gather(const S* __restrict__ src, int x, int y, int z, const PR<typename Codec<S>::R>& p,
                                        typename Codec<S>::R (&h)[Lat<D>::Q]) {
     if constexpr (WALLS) {
         const bool near = (p.bc[0] == 1 && (x == 0 || x == p.nx - 1)) || (p.bc[1] == 1 && (y == 0 || y == p.ny - 1)) ||
                           (D == 3 && p.bc[2] == 1 && (z == 0 || z == p.nz - 1));
-        if (near) gather_impl<D, S, true, BIG>(src, x, y, z, p, h);
-        else gather_impl<D, S, false, BIG>(src, x, y, z, p, h);
+        if (near) gather_impl<D, S, true, BIG, WEIGHTED>(src, x, y, z, p, h);
+        else gather_impl<D, S, false, BIG, WEIGHTED>(src, x, y, z, p, h);
     } else {
-        gather_impl<D, S, false, BIG>(src, x, y, z, p, h);
+        gather_impl<D, S, false, BIG, WEIGHTED>(src, x, y, z, p, h);
     }
 }
 
@@ -499,57 +511,59 @@ __device__ __forceinline__ Hydro<D, R> hydro(const R (&h)[Lat<D>::Q], const R F[
     return o;
 }
 
-// The collision's first pass over the populations: the raw moments of every x-line (three
-// populations with e_x = -1, 0, +1): (sum, sum e_x, sum e_x^2), in place. The hydrodynamic
-// fields are sums of these, and the x-sweep of the central transform continues from them.
+// The collision reads the stored deviations d = h / w. The weights are products of the 1D
+// weights w1(e) = r1(e) / 6 with r1 = (1, 4, 1) for e = (-1, 0, +1), so every moment of h is
+// 6^-D times the same moment of r d, r = prod r1. The sweeps below weight by r1 (a multiply-add
+// by 4 in place of an add: no product per population), and the collision applies 6^-D where
+// it reads a moment (moment_scale).
+template <int D> __host__ __device__ constexpr double moment_scale() { return D == 3 ? 1.0 / 216.0 : 1.0 / 36.0; }
+
+// The first pass: the r1-weighted raw moments of every x-line (three deviations with
+// e_x = -1, 0, +1): (sum r1 d, sum r1 d e_x, sum r1 d e_x^2), in place. The hydrodynamic fields
+// are sums of these, and the x-sweep of the central transform continues from them.
 template <int D, class R> __device__ __forceinline__ void raw_x(R (&m)[Lat<D>::Q]) {
     constexpr int NL = Lat<D>::Q / 3;
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
         const R a = m[3 * l], b = m[3 * l + 1], c = m[3 * l + 2];
         const R s1 = c - a, s2 = c + a;
-        m[3 * l] = s2 + b;
+        m[3 * l] = fma(R(4), b, s2);
         m[3 * l + 1] = s1;
         m[3 * l + 2] = s2;
     }
 }
 
-// The same raw x-line moments of h = w d from the stored deviations d: on a line the two
-// e_x = -+1 weights are equal (w_e) and the e_x = 0 weight is 4 w_e, so
-// (sum, sum e_x, sum e_x^2) = (w_0 d_0 + w_e (d_+ + d_-), w_e (d_+ - d_-), w_e (d_+ + d_-)):
-// five operations per line instead of three weight products and three sums.
-template <int D, class R> __device__ __forceinline__ void raw_x_dev(R (&m)[Lat<D>::Q]) {
-    constexpr int NL = Lat<D>::Q / 3;
-    sfor<NL>([&](auto LI) {
-        constexpr int l = decltype(LI)::value;
-        constexpr scalar_t<R> we = (scalar_t<R>)weight_slot<D>(3 * l), w0 = (scalar_t<R>)weight_slot<D>(3 * l + 1);
-        const R a = m[3 * l], b = m[3 * l + 1], c = m[3 * l + 2];
-        const R s2 = (c + a) * R(we);
-        m[3 * l + 1] = (c - a) * R(we);
-        m[3 * l + 2] = s2;
-        m[3 * l] = fma(R(w0), b, s2);
-    });
-}
-
-// rho - 1 and the momentum (Eqs. densitycalculation, velocitycalculation) from the raw x-line
-// moments: line l = (e_y + 1) + 3 (e_z + 1)
+// rho - 1 and the momentum (Eqs. densitycalculation, velocitycalculation) from the x-line
+// moments of raw_x(): line l = (e_y + 1) + 3 (e_z + 1) carries the weight r1(e_y) r1(e_z), so
+// the sums over e_y (per e_z) and then over e_z are again multiply-adds by 4
 template <int D, class R, bool GEN = true, bool FORCED = true, bool FYZ = true, bool RED = false>
 __device__ __forceinline__ Hydro<D, R> hydro_x(const R (&m)[Lat<D>::Q], const R F[3], const PR<scalar_t<R>>& p) {
-    constexpr int NL = Lat<D>::Q / 3;
-    Hydro<D, R> o;
-    R drho = m[0], jx = m[1];
+    using T = scalar_t<R>;
+    constexpr int NZ = Lat<D>::NZ;
+    const R C = R((T)moment_scale<D>());
+    R A[NZ], B[NZ], Y[NZ];
 #pragma unroll
-    for (int l = 1; l < NL; ++l) {
-        drho += m[3 * l];
-        jx += m[3 * l + 1];
+    for (int c = 0; c < NZ; ++c) {
+        const int l0 = 3 * c, l1 = 3 * c + 1, l2 = 3 * c + 2;      // e_y = -1, 0, +1
+        A[c] = fma(R(4), m[3 * l1], m[3 * l0] + m[3 * l2]);
+        B[c] = fma(R(4), m[3 * l1 + 1], m[3 * l0 + 1] + m[3 * l2 + 1]);
+        Y[c] = m[3 * l2] - m[3 * l0];
     }
-    R jy = R(0), jz = R(0);
-#pragma unroll
-    for (int c = 0; c < NL / 3; ++c) jy += m[3 * (3 * c + 2)] - m[3 * (3 * c)];
+    R drho, jx, jy, jz = R(0);
     if constexpr (D == 3) {
-#pragma unroll
-        for (int b = 0; b < 3; ++b) jz += m[3 * (6 + b)] - m[3 * b];
+        drho = fma(R(4), A[1], A[0] + A[2]);
+        jx = fma(R(4), B[1], B[0] + B[2]);
+        jy = fma(R(4), Y[1], Y[0] + Y[2]);
+        jz = (A[2] - A[0]) * C;
+    } else {
+        drho = A[0];
+        jx = B[0];
+        jy = Y[0];
     }
+    drho = drho * C;
+    jx = jx * C;
+    jy = jy * C;
+    Hydro<D, R> o;
     o.drho = drho;
     if constexpr (FORCED) {
         o.jx = fma(R(0.5), F[0], jx);
@@ -587,7 +601,7 @@ __device__ __forceinline__ void central_forward(R (&m)[Lat<D>::Q], R ux, R uy, R
 
 // The forward transform continued from the raw x-line moments of raw_x(): shift the x-moments
 // to central ones about u_x, (m0, s1, s2) -> (m0, s1 - u m0, s2 - 2u s1 + u^2 m0), then the
-// y and z sweeps. Equal to central_forward() on the populations.
+// y and z sweeps (r1-weighted): 6^D times central_forward() on the populations h = w d.
 template <int D, class R>
 __device__ __forceinline__ void central_forward_from_x(R (&m)[Lat<D>::Q], R ux, R uy, R uz) {
     constexpr int NL = Lat<D>::Q / 3;
@@ -602,10 +616,10 @@ __device__ __forceinline__ void central_forward_from_x(R (&m)[Lat<D>::Q], R ux, 
 #pragma unroll
     for (int c = 0; c < Lat<D>::NZ; ++c)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) fwd1(m[9 * c + a], m[9 * c + 3 + a], m[9 * c + 6 + a], ny, ty, qy);
+        for (int a = 0; a < 3; ++a) fwd1r(m[9 * c + a], m[9 * c + 3 + a], m[9 * c + 6 + a], ny, ty, qy);
     if constexpr (D == 3) {
 #pragma unroll
-        for (int t = 0; t < 9; ++t) fwd1(m[t], m[9 + t], m[18 + t], nz, tz, qz);
+        for (int t = 0; t < 9; ++t) fwd1r(m[t], m[9 + t], m[18 + t], nz, tz, qz);
     }
 }
 
@@ -693,11 +707,11 @@ template <class R, int a, int b, int c> __device__ __forceinline__ R weight_cm(c
 
 // ------------------------------------------------------------------------------------------
 // The collision in central-moment space (generic form; see the file header and cmlbm.h).
-// In: h deviation populations (slot order), force F, the eddy-viscosity constant cs_eff (0 = off).
-// Out: h holds the post-collision deviation populations h, each scaled by 2^n (n = |e_x| + |e_y|
-// + |e_z| of its direction, see central_inverse_impl): the caller stores h * inv_weight_scaled.
-// With DEV the populations come in and go out as the stored deviations d = h / w (the weights
-// folded into the first and last sweeps).
+// In: the stored deviations d = h / w (slot order; h = fbar - w), force F, the eddy-viscosity
+// constant cs_eff (0 = off); the weights enter the sweeps as relative factors (raw_x).
+// Out: with DEV the post-collision deviations d (the inverse weights folded into the last
+// sweep); otherwise the deviation populations h, each scaled by 2^n (n = |e_x| + |e_y| + |e_z|
+// of its direction, see central_inverse_impl), which the caller stores as h * inv_weight_scaled.
 // R is the arithmetic type (double, float, or F2 for two cells of one row; cs_eff and the
 // parameters are then scalars shared by both cells).
 // ------------------------------------------------------------------------------------------
@@ -705,12 +719,25 @@ template <int D, class R, class FT, bool DEV = false>
 __device__ __forceinline__ void collide(R (&m)[Lat<D>::Q], const R F[3], const PR<scalar_t<R>>& p, scalar_t<R> cs_eff) {
     using T = scalar_t<R>;
     constexpr int Q = Lat<D>::Q;
-    if constexpr (DEV) raw_x_dev<D, R>(m);
-    else raw_x<D, R>(m);
+    raw_x<D, R>(m);
     const Hydro<D, R> hy = hydro_x<D, R, FT::GEN, !FT::SIMPLE, !FT::FX, FT::RED>(m, F, p);
     const R drho = hy.drho, rho = R(1) + hy.drho, ndrho = -hy.drho;
     const R u[3] = {hy.ux, hy.uy, hy.uz};
     central_forward_from_x<D, R>(m, u[0], u[1], u[2]);
+    const R C = R((T)moment_scale<D>());        // m holds 6^D times the central moments of h
+    // zeroth and first order leave the collision at once (their pre-collision central moments
+    // are not read): the density deviation, and the momentum plus the source sigma_x = F_x
+    // (collision invariants), as central moments about u
+    m[0] = drho;
+    if constexpr (FT::SIMPLE) {
+        m[midx(1, 0, 0)] = fma(ndrho, u[0], hy.jx);
+        m[midx(0, 1, 0)] = fma(ndrho, u[1], hy.jy);
+        if constexpr (D == 3) m[midx(0, 0, 1)] = fma(ndrho, u[2], hy.jz);
+    } else {
+        m[midx(1, 0, 0)] = fma(ndrho, u[0], fma(R(0.5), F[0], hy.jx));
+        m[midx(0, 1, 0)] = fma(ndrho, u[1], FT::FX ? hy.jy : fma(R(0.5), F[1], hy.jy));
+        if constexpr (D == 3) m[midx(0, 0, 1)] = fma(ndrho, u[2], FT::FX ? hy.jz : fma(R(0.5), F[2], hy.jz));
+    }
 
     const R third = R(T(1) / 3);
     const R q[3] = {u[0] * u[0], u[1] * u[1], u[2] * u[2]};
@@ -722,14 +749,14 @@ __device__ __forceinline__ void collide(R (&m)[Lat<D>::Q], const R F[3], const P
     const R Fr2[3] = {Fr[0] + Fr[0], Fr[1] + Fr[1], Fr[2] + Fr[2]};
 
     // second order: non-equilibrium stress Pi = kappa - c_s^2 rho delta (kappa = kbar at order 2)
-    const R Pxx = m[midx(2, 0, 0)] + fma(ndrho, third, q[0]);
-    const R Pyy = m[midx(0, 2, 0)] + fma(ndrho, third, q[1]);
-    const R Pxy = fma(u[0], u[1], m[midx(1, 1, 0)]);
+    const R Pxx = fma(m[midx(2, 0, 0)], C, fma(ndrho, third, q[0]));
+    const R Pyy = fma(m[midx(0, 2, 0)], C, fma(ndrho, third, q[1]));
+    const R Pxy = fma(m[midx(1, 1, 0)], C, u[0] * u[1]);
     R Pzz = R(0), Pxz = R(0), Pyz = R(0);
     if constexpr (D == 3) {
-        Pzz = m[midx(0, 0, 2)] + fma(ndrho, third, q[2]);
-        Pxz = fma(u[0], u[2], m[midx(1, 0, 1)]);
-        Pyz = fma(u[1], u[2], m[midx(0, 1, 1)]);
+        Pzz = fma(m[midx(0, 0, 2)], C, fma(ndrho, third, q[2]));
+        Pxz = fma(m[midx(1, 0, 1)], C, u[0] * u[2]);
+        Pyz = fma(m[midx(0, 1, 1)], C, u[1] * u[2]);
     }
 
     R wnu;
@@ -844,8 +871,8 @@ __device__ __forceinline__ void collide(R (&m)[Lat<D>::Q], const R F[3], const P
                     const R hs = R(0.5) * s;
                     const R kw = weight_cm<R, a, b, c>(cw);
                     if constexpr (ord(t) < 2 * D) {
-                        if constexpr (sourced) kap[t] = fma(R(0.5), s, m[t] + kw);
-                        else kap[t] = m[t] + kw;
+                        if constexpr (sourced) kap[t] = fma(R(0.5), s, fma(m[t], C, kw));
+                        else kap[t] = fma(m[t], C, kw);
                     }
                     constexpr bool even = (a % 2 == 0) && (b % 2 == 0) && (c % 2 == 0);
                     constexpr int twos = (a == 2) + (b == 2) + (c == 2);
@@ -867,7 +894,7 @@ __device__ __forceinline__ void collide(R (&m)[Lat<D>::Q], const R F[3], const P
                     } else {
                         const R w = (ord(t) == 3) ? w3 : w4;
                         const R om = (ord(t) == 3) ? om3 : om4;
-                        m[t] = fma(om, m[t] + hs, fma(w, DM, hs));
+                        m[t] = fma(om, fma(m[t], C, hs), fma(w, DM, hs));
                     }
                 }
             });
@@ -883,17 +910,6 @@ __device__ __forceinline__ void collide(R (&m)[Lat<D>::Q], const R F[3], const P
         m[midx(1, 0, 1)] = fma(-u[0], u[2], Txz);
         m[midx(0, 1, 1)] = fma(-u[1], u[2], Tyz);
     }
-    // first order: collision invariant plus the source sigma_x = F_x
-    if constexpr (FT::SIMPLE) {
-        m[midx(1, 0, 0)] = fma(ndrho, u[0], hy.jx);
-        m[midx(0, 1, 0)] = fma(ndrho, u[1], hy.jy);
-        if constexpr (D == 3) m[midx(0, 0, 1)] = fma(ndrho, u[2], hy.jz);
-    } else {
-        m[midx(1, 0, 0)] = fma(ndrho, u[0], fma(R(0.5), F[0], hy.jx));
-        m[midx(0, 1, 0)] = fma(ndrho, u[1], FT::FX ? hy.jy : fma(R(0.5), F[1], hy.jy));
-        if constexpr (D == 3) m[midx(0, 0, 1)] = fma(ndrho, u[2], FT::FX ? hy.jz : fma(R(0.5), F[2], hy.jz));
-    }
-    // zeroth order unchanged (m[0] = drho)
 
     central_inverse_impl<D, R, DEV ? kInvDev : kInvScaled>(m, u[0], u[1], u[2]);
 }

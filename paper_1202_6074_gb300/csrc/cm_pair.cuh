@@ -48,9 +48,10 @@ constexpr int pair_min_blocks() {
 // but -1 % for the unforced FP32 step, which stays on (x, x + nx/2).
 template <class S, class FT> constexpr bool pair_adjacent() { return sizeof(S) == 2 || !FT::SIMPLE; }
 
-// Whether the collision takes and returns the stored deviations with the weights folded into its
-// first and last sweeps (collide<..., DEV>), or multiplies by the weights on the way in and out.
-// Measured at 256^3: +1 % (Taylor-Green BF16/FP16) and +2.4 % (channel BF16) with the folded
+// Whether the collision returns the stored deviations with the inverse weights folded into its
+// last sweep (collide<..., DEV>), or 2^n h, which the store multiplies by 1 / (2^n w) (the
+// collision takes the stored deviations either way). Measured at 256^3 when the choice also
+// applied on the way in: +1 % (Taylor-Green BF16/FP16) and +2.4 % (channel BF16) with the folded
 // weights, but -0.7 % with a force field (isotropic LES BF16) and -0.2 % for the unforced FP32
 // step; the FP32 steps and the force-field steps keep the explicit weights.
 template <class S, class FT> __host__ __device__ constexpr bool pair_dev() {
@@ -307,12 +308,6 @@ __global__ void __launch_bounds__(kBlock, pair_min_blocks<S, FT>()) k_step_pair(
         for (int d = 0; d < 3; ++d) F[d] = F2(p.F[d]);
     }
     constexpr bool DEV = pair_dev<S, FT>();
-    if constexpr (!DEV) {
-        sfor<27>([&](auto I) {
-            constexpr int t = decltype(I)::value;
-            h[t] = h[t] * F2((float)weight_slot<3>(t));
-        });
-    }
     collide<3, F2, FT, DEV>(h, F, p, smagorinsky_constant<float, FT::LES>(p, y));
     sfor<27>([&](auto I) {
         constexpr int i = decltype(I)::value;

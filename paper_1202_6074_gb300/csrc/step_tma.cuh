@@ -196,7 +196,6 @@ __global__ void __launch_bounds__(TX + 32, 2) k_step_tma(const __grid_constant__
         sfor<Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
             constexpr int ex = Lat<3>::ex(i), ey = Lat<3>::ey(i), ez = Lat<3>::ez(i);
-            constexpr R w = (R)weight<3>(i);
             const int j = tid - ex;       // position in the staged row; -1 and TX are the halos
             const S* ptr = main_row(s, i) + j;
             if constexpr (HALO) {
@@ -222,7 +221,7 @@ __global__ void __launch_bounds__(TX + 32, 2) k_step_tma(const __grid_constant__
                     }
                 }
             }
-            h[slot<3>(i)] = d * w;
+            h[slot<3>(i)] = d;
         });
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
