@@ -26,9 +26,6 @@ namespace cm {
 #ifndef CM_PAIR_FIELD_UNIT_BLOCKS
 #define CM_PAIR_FIELD_UNIT_BLOCKS (CM_PAIR_MIN_BLOCKS + 1)
 #endif
-#ifndef CM_PAIR_FIELD_DEV
-#define CM_PAIR_FIELD_DEV 0
-#endif
 template <class S, class FT>
 constexpr int pair_min_blocks() {
     if constexpr (sizeof(S) == 2) {
@@ -50,13 +47,10 @@ template <class S, class FT> constexpr bool pair_adjacent() { return sizeof(S) =
 
 // Whether the collision returns the stored deviations with the inverse weights folded into its
 // last sweep (collide<..., DEV>), or 2^n h, which the store multiplies by 1 / (2^n w) (the
-// collision takes the stored deviations either way). Measured at 256^3 when the choice also
-// applied on the way in: +1 % (Taylor-Green BF16/FP16) and +2.4 % (channel BF16) with the folded
-// weights, but -0.7 % with a force field (isotropic LES BF16) and -0.2 % for the unforced FP32
-// step; the FP32 steps and the force-field steps keep the explicit weights.
-template <class S, class FT> __host__ __device__ constexpr bool pair_dev() {
-    return sizeof(S) == 2 && (!FT::FIELD || CM_PAIR_FIELD_DEV);
-}
+// collision takes the stored deviations either way). The 16-bit steps, which are bound by
+// their FP32 arithmetic, fold (the force-field LES BF16 step: +2.2 % at 512^3); the FP32 steps,
+// bound by HBM, keep the product at the store.
+template <class S, class FT> __host__ __device__ constexpr bool pair_dev() { return sizeof(S) == 2; }
 
 // Plane ring of the two-steps-per-pass schedule (launch_pair_two_steps): the intermediate state
 // t+1 lives in a small buffer of z-planes instead of a full state buffer. Plane z sits in slot
