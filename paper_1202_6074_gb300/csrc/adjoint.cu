@@ -257,14 +257,19 @@ __global__ void __launch_bounds__(kBlock, CM_ADJ_MIN_BLOCKS) k_adjoint_step(cons
     });
     R F[3];
     load_force<R>(Ff, p, cell, F);
+    // rho and sum g e: the e = 0 terms are left out (a product by zero is not removed by the
+    // compiler: it would change the sign of a zero sum)
     R rho = 0, jx = 0, jy = 0, jz = 0;
-#pragma unroll
-    for (int t = 0; t < Q; ++t) {
+    sfor<Q>([&](auto TI) {
+        constexpr int t = decltype(TI)::value;
         rho += A[t];
-        jx += R(ex_a(t) - 1) * A[t];
-        jy += R(ex_b(t) - 1) * A[t];
-        if constexpr (D == 3) jz += R(ex_c(t) - 1) * A[t];
-    }
+        if constexpr (ex_a(t) == 2) jx += A[t];
+        if constexpr (ex_a(t) == 0) jx -= A[t];
+        if constexpr (ex_b(t) == 2) jy += A[t];
+        if constexpr (ex_b(t) == 0) jy -= A[t];
+        if constexpr (D == 3 && ex_c(t) == 2) jz += A[t];
+        if constexpr (D == 3 && ex_c(t) == 0) jz -= A[t];
+    });
     const R irho = rcp(rho);
     const R u[3] = {(jx + R(0.5) * F[0]) * irho, (jy + R(0.5) * F[1]) * irho, D == 3 ? (jz + R(0.5) * F[2]) * irho : R(0)};
     central_forward<D, R>(A, u[0], u[1], u[2]);      // A = kbar
