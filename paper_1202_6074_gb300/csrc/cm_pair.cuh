@@ -66,8 +66,8 @@ struct Ring {
     }
 };
 
-// The pair gathers return the stored deviations d (moving-wall term included), not h = w d
-// (see pair_dev).
+// The pair gathers return the stored deviations d (moving-wall term included), not h = w d:
+// the collision takes them as they are (see collide).
 // RS / RD: the source / destination state is the ring (else a full buffer with stride p.S)
 template <class S, bool WALLS, bool RS = false, bool BIG = false>
 __device__ __forceinline__ void gather_pair(const S* __restrict__ src, int x, int y, int z, const PR<float>& p, F2 (&h)[27],
