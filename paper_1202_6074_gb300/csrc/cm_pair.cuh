@@ -14,14 +14,21 @@ namespace cm {
 #endif
 // Resident blocks per SM the register budget is sized for. The 16-bit steps are bound by
 // instruction latency rather than by HBM and gain from more resident warps where the registers
-// allow: 6 blocks (at most 80 registers, a 4-byte spill) for the unforced SIMPLE collision,
-// +2 %; 5 (at most 96) for forced steps without a force field (+5 % on the channel) and for
-// the UNIT collision with a force field (+1.6 % on the isotropic turbulence LES). The general
-// relaxation with a force field loses 1 % at 5 blocks and stays at 4 (at most 128 registers),
-// as do the general forms (they spill twice as much at 5) and all FP32 steps (the forced FP32
-// LES loses 7 % at 5).
+// allow:
+//   6 blocks (at most 80 registers) for the unforced SIMPLE collision: +2 % over 5, while 7
+//     (72 registers, a 76-byte spill) lose 3 %;
+//   6 for the uniform force along x (FX): +1.5 % over 5;
+//   5 (at most 96) for the other forced steps without a force field (+5 % on the channel) and
+//     for the UNIT collision with a force field (+1.6 % on the isotropic turbulence LES; at 6
+//     it would spill over 200 bytes).
+// The general relaxation with a force field loses 1 % at 5 blocks and stays at 4 (at most 128
+// registers), as do the general forms (they spill twice as much at 5) and all FP32 steps (the
+// forced FP32 LES loses 7 % at 5).
 #ifndef CM_PAIR_FX_BLOCKS
 #define CM_PAIR_FX_BLOCKS (CM_PAIR_MIN_BLOCKS + 2)
+#endif
+#ifndef CM_PAIR_SIMPLE_BLOCKS
+#define CM_PAIR_SIMPLE_BLOCKS (CM_PAIR_MIN_BLOCKS + 2)
 #endif
 #ifndef CM_PAIR_FIELD_UNIT_BLOCKS
 #define CM_PAIR_FIELD_UNIT_BLOCKS (CM_PAIR_MIN_BLOCKS + 1)
@@ -31,7 +38,7 @@ constexpr int pair_min_blocks() {
     if constexpr (sizeof(S) == 2) {
         if constexpr (FT::FX) return CM_PAIR_FX_BLOCKS;
         if constexpr (FT::FIELD && FT::UNIT && !FT::GEN) return CM_PAIR_FIELD_UNIT_BLOCKS;
-        return FT::SIMPLE ? CM_PAIR_MIN_BLOCKS + 2
+        return FT::SIMPLE ? CM_PAIR_SIMPLE_BLOCKS
                           : (!FT::GEN && (!FT::FIELD || FT::UNIT) ? CM_PAIR_MIN_BLOCKS + 1 : CM_PAIR_MIN_BLOCKS);
     }
     return CM_PAIR_MIN_BLOCKS;
@@ -263,8 +270,8 @@ __global__ void __launch_bounds__(kBlock, pair_min_blocks<S, FT>()) k_step_pair(
         // warps are 32 consecutive threads of one row (blockDim.x is a multiple of 32): the warp
         // covers columns 2 x_w .. 2 x_w + 63, and pulls across the periodic x edge only if it holds
         // the row's first or last pair (the test is warp-uniform). The immediate-offset gather of
-        // such interior warps measured +1.5 % for the FX channel variant and -2.5 % for the others
-        // (the 512^3 force-field LES, the unforced Taylor-Green step), which keep gather_adj.
+        // such interior warps measured +1.5 % for the FX channel variant, but -7 % for the 512^3
+        // force-field LES and -2.3 % for the unforced Taylor-Green step, which keep gather_adj.
         const int xw = x - (int)(threadIdx.x & 31u);
         const bool inner = FT::FX && xw > 0 && 2 * (xw + 31) + 2 < p.nx;
         bool near = false;
