@@ -70,6 +70,7 @@ template <class R> struct PR {
     unsigned long long N64, S64;   // the same as 64-bit values (kernels with 64-bit offsets)
     int wz;                // z wrap length: nz, or 0 on a slab (the ghost planes are read instead)
     R uw[3][2][3];
+    int moving;            // some wall velocity is non-zero (else the pull adds no wall term)
     R F[3];
     R tau0, omega_bulk, omega3, omega4, cs, vd_aplus, vd_utau_nu, rho0;
     R omega_nu;            // 1 / tau0, IEEE-rounded on the host (used by the FP64 collision)
@@ -89,6 +90,10 @@ template <class R> inline PR<R> typed(const Params& p) {
     for (int a = 0; a < 3; ++a)
         for (int s = 0; s < 2; ++s)
             for (int d = 0; d < 3; ++d) q.uw[a][s][d] = (R)p.uw[a][s][d];
+    q.moving = 0;
+    for (int a = 0; a < 3; ++a)
+        for (int s = 0; s < 2; ++s)
+            for (int d = 0; d < 3; ++d) q.moving |= p.uw[a][s][d] != 0.0;
     for (int d = 0; d < 3; ++d) q.F[d] = (R)p.F[d];
     q.tau0 = (R)p.tau0; q.omega_bulk = (R)p.omega_bulk; q.omega3 = (R)p.omega3; q.omega4 = (R)p.omega4;
     q.cs = (R)p.cs; q.vd_aplus = (R)p.vd_aplus; q.vd_utau_nu = (R)p.vd_utau_nu; q.rho0 = (R)p.rho0;
@@ -380,6 +385,28 @@ template <class R> __device__ __forceinline__ void inv1x2(R& a, R& b, R& c, R u,
     c = r2 + r1;
 }
 
+// e_i . u_w of direction i with the wall velocity w, the zero components of e_i left out at
+// compile time (the compiler keeps a product by zero: it could change the sign of a zero sum)
+template <int D, int i, class R> __device__ __forceinline__ R e_dot(const R (&w)[3]) {
+    constexpr int ex = Lat<D>::ex(i), ey = Lat<D>::ey(i), ez = Lat<D>::ez(i);
+    static_assert(ex != 0 || ey != 0 || ez != 0, "the rest population crosses no wall");
+    R r = R(0);
+    if constexpr (ex != 0) r = ex > 0 ? w[0] : -w[0];
+    if constexpr (ey != 0) {
+        if constexpr (ex != 0) r = ey > 0 ? r + w[1] : r - w[1];
+        else r = ey > 0 ? w[1] : -w[1];
+    }
+    if constexpr (ez != 0) {
+        if constexpr (ex != 0 || ey != 0) r = ez > 0 ? r + w[2] : r - w[2];
+        else r = ez > 0 ? w[2] : -w[2];
+    }
+    return r;
+}
+// 6 / (number of walls a link crosses: 1, 2 at an edge, 3 at a corner) of the moving-wall term
+template <class R> __device__ __forceinline__ R wall_factor(int cnt) {
+    return cnt >= 3 ? R(2) : cnt == 2 ? R(3) : R(6);
+}
+
 // ------------------------------------------------------------------------------------------
 // Pull with periodic wrap and half-way bounce-back; fills h (slot order) with the deviation
 // populations h = w d, or with WEIGHTED = false the stored deviations d themselves
@@ -436,14 +463,16 @@ __device__ __forceinline__ void gather_impl(const S* __restrict__ src, int x, in
             const IX own = IX(Lat<D>::opp(i)) * PS + cell;
             const IX pulled = IX(i) * PS + row[c][b] + (unsigned)xs[a];
             R d = Codec<S>::ld(src + (bounced ? own : pulled));
-            constexpr int sx = (a == 2) ? 0 : 1, sy = (b == 2) ? 0 : 1, sz = (c == 2) ? 0 : 1;
-            R eu = R(0);
-            if constexpr (a != 1) eu += bx ? (R(Lat<D>::ex(i)) * p.uw[0][sx][0] + R(Lat<D>::ey(i)) * p.uw[0][sx][1] + R(Lat<D>::ez(i)) * p.uw[0][sx][2]) : R(0);
-            if constexpr (b != 1) eu += by ? (R(Lat<D>::ex(i)) * p.uw[1][sy][0] + R(Lat<D>::ey(i)) * p.uw[1][sy][1] + R(Lat<D>::ez(i)) * p.uw[1][sy][2]) : R(0);
-            if constexpr (c != 1) eu += bz ? (R(Lat<D>::ex(i)) * p.uw[2][sz][0] + R(Lat<D>::ey(i)) * p.uw[2][sz][1] + R(Lat<D>::ez(i)) * p.uw[2][sz][2]) : R(0);
-            const int cnt = (int)bx + (int)by + (int)bz;
-            const R inv_cnt = cnt >= 3 ? R(1) / 3 : cnt == 2 ? R(0.5) : R(1);
-            d += R(6) * eu * inv_cnt;
+            if (p.moving) {
+                // half-way bounce-back from a moving wall: d += 6 (e . u_w), averaged over the
+                // walls the link crosses
+                constexpr int sx = (a == 2) ? 0 : 1, sy = (b == 2) ? 0 : 1, sz = (c == 2) ? 0 : 1;
+                R eu = R(0);
+                if constexpr (a != 1) eu = bx ? eu + e_dot<D, i>(p.uw[0][sx]) : eu;
+                if constexpr (b != 1) eu = by ? eu + e_dot<D, i>(p.uw[1][sy]) : eu;
+                if constexpr (c != 1) eu = bz ? eu + e_dot<D, i>(p.uw[2][sz]) : eu;
+                d = fma(wall_factor<R>((int)bx + (int)by + (int)bz), eu, d);
+            }
             h[slot<D>(i)] = WEIGHTED ? d * w : d;
         } else {
             const R d = Codec<S>::ld(src + (IX(i) * PS + row[c][b] + (unsigned)xs[a]));

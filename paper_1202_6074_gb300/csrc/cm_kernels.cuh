@@ -209,8 +209,8 @@ inline bool has_walls(const Params& p) { return p.bc[0] == 1 || p.bc[1] == 1 || 
 template <int D, class S, class FT>
 void launch_step_ft(const void* src, void* dst, const void* Ff, const Params& p, cudaStream_t st) {
     using R = typename Codec<S>::R;
-    if constexpr (FT::UNIT) {           // only dispatched to the two-cells-per-thread kernel
-        static_assert(D == 3 && sizeof(R) == 4, "UNIT variants are pair-kernel variants");
+    if constexpr (FT::UNIT && D == 3) {     // the D3Q27 UNIT variants are pair-kernel variants
+        static_assert(sizeof(R) == 4, "D3Q27 UNIT variants are pair-kernel variants");
         launch_pair<S, FT>(src, dst, Ff, p, st);
         return;
     } else if constexpr (D == 3 && sizeof(R) == 4) {
@@ -268,6 +268,15 @@ void launch_step_g(const void* src, void* dst, const void* Ff, const Params& p, 
                     return;
                 }
             }
+            launch_step_ft<D, S, Feat<W, L, F, false, false, true>>(src, dst, Ff, p, st);
+            return;
+        }
+    }
+    if constexpr (D == 2 && sizeof(R) == 8) {
+        // the D2Q9 FP64 step on small grids is bound by the chain of FP64 operations of its
+        // collision (GB300's FP64 pipe takes about 64 cycles per warp instruction): with unit
+        // higher-order rates the relaxation of orders 3 and 4 drops its products by the rates
+        if (p.omega3 == 1.0 && p.omega4 == 1.0) {
             launch_step_ft<D, S, Feat<W, L, F, false, false, true>>(src, dst, Ff, p, st);
             return;
         }

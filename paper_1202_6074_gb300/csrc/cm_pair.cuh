@@ -130,15 +130,18 @@ __device__ __forceinline__ void gather_pair(const S* __restrict__ src, int x, in
             const bool by = yo[b], bz = zo[c];
             const bool bounced = by || bz;
             const IX own = IX(Lat<3>::opp(i)) * PS;
-            const float da = Codec<S>::ld(src + (bounced ? own + cellA : base + (unsigned)xa[a]));
-            const float db = Codec<S>::ld(src + (bounced ? own + cellB : base + (unsigned)xb[a]));
-            constexpr int sy = (b == 2) ? 0 : 1, sz = (c == 2) ? 0 : 1;
-            float eu = 0.f;
-            if constexpr (b != 1) eu += by ? (float(Lat<3>::ex(i)) * p.uw[1][sy][0] + float(Lat<3>::ey(i)) * p.uw[1][sy][1] + float(Lat<3>::ez(i)) * p.uw[1][sy][2]) : 0.f;
-            if constexpr (c != 1) eu += bz ? (float(Lat<3>::ex(i)) * p.uw[2][sz][0] + float(Lat<3>::ey(i)) * p.uw[2][sz][1] + float(Lat<3>::ez(i)) * p.uw[2][sz][2]) : 0.f;
-            const int cnt = (int)by + (int)bz;
-            const float add = 6.f * eu * (cnt == 2 ? 0.5f : 1.f);
-            h[slot<3>(i)] = F2(da + add, db + add);
+            float da = Codec<S>::ld(src + (bounced ? own + cellA : base + (unsigned)xa[a]));
+            float db = Codec<S>::ld(src + (bounced ? own + cellB : base + (unsigned)xb[a]));
+            if (p.moving) {       // half-way bounce-back from a moving wall (see gather_impl)
+                constexpr int sy = (b == 2) ? 0 : 1, sz = (c == 2) ? 0 : 1;
+                float eu = 0.f;
+                if constexpr (b != 1) eu = by ? eu + e_dot<3, i>(p.uw[1][sy]) : eu;
+                if constexpr (c != 1) eu = bz ? eu + e_dot<3, i>(p.uw[2][sz]) : eu;
+                const float k = wall_factor<float>((int)by + (int)bz);
+                da = fmaf(k, eu, da);
+                db = fmaf(k, eu, db);
+            }
+            h[slot<3>(i)] = F2(da, db);
         } else {
             if constexpr (sizeof(S) == 2)   // 64-bit row pointers (measured faster at 16-bit storage)
                 h[slot<3>(i)] = F2(Codec<S>::ld(src + xa[a] + base), Codec<S>::ld(src + xb[a] + base));
@@ -196,13 +199,16 @@ __device__ __forceinline__ void gather_adj(const S* __restrict__ src, int x0, in
                 d.x = Codec<S>::ld(src + (bounced ? back : base + (unsigned)c0[a]));
                 d.y = Codec<S>::ld(src + (bounced ? back + 1u : base + (unsigned)c1[a]));
             }
-            constexpr int sy = (b == 2) ? 0 : 1, sz = (c == 2) ? 0 : 1;
-            float eu = 0.f;
-            if constexpr (b != 1) eu += by ? (float(Lat<3>::ex(i)) * p.uw[1][sy][0] + float(Lat<3>::ey(i)) * p.uw[1][sy][1] + float(Lat<3>::ez(i)) * p.uw[1][sy][2]) : 0.f;
-            if constexpr (c != 1) eu += bz ? (float(Lat<3>::ex(i)) * p.uw[2][sz][0] + float(Lat<3>::ey(i)) * p.uw[2][sz][1] + float(Lat<3>::ez(i)) * p.uw[2][sz][2]) : 0.f;
-            const int cnt = (int)by + (int)bz;
-            const float add = 6.f * eu * (cnt == 2 ? 0.5f : 1.f);
-            h[slot<3>(i)] = F2(d.x + add, d.y + add);
+            if (p.moving) {       // half-way bounce-back from a moving wall (see gather_impl)
+                constexpr int sy = (b == 2) ? 0 : 1, sz = (c == 2) ? 0 : 1;
+                float eu = 0.f;
+                if constexpr (b != 1) eu = by ? eu + e_dot<3, i>(p.uw[1][sy]) : eu;
+                if constexpr (c != 1) eu = bz ? eu + e_dot<3, i>(p.uw[2][sz]) : eu;
+                const float k = wall_factor<float>((int)by + (int)bz);
+                d.x = fmaf(k, eu, d.x);
+                d.y = fmaf(k, eu, d.y);
+            }
+            h[slot<3>(i)] = F2(d.x, d.y);
         } else if constexpr (a == 1) {
             const float2 d = Codec<S>::ld2(src + x0 + base);
             h[slot<3>(i)] = F2(d.x, d.y);
