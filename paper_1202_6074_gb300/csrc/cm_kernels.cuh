@@ -75,11 +75,11 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S>()) k_step(const S* 
     gather<D, S, FT::WALLS, FT::BIG, false>(src, x, y, z, p, h);
     R F[3];
     load_force<R, FT::FIELD, FT::BIG>(Ff, p, cell, F);
-    collide<D, R, FT>(h, F, p, smagorinsky_constant<R, FT::LES>(p, y));
+    // the collision returns the stored deviations (inverse weights folded into its last sweep)
+    collide<D, R, FT, true>(h, F, p, smagorinsky_constant<R, FT::LES>(p, y));
     sfor<Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        constexpr R iw = (R)inv_weight_scaled<D>(i);
-        Codec<S>::st(dst + (IX(i) * PS + cell), h[slot<D>(i)] * iw);
+        Codec<S>::st(dst + (IX(i) * PS + cell), h[slot<D>(i)]);
     });
 }
 
