@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--flow", default="tgv", choices=["tgv", "hit"],
                     help="timed workload: the Taylor-Green vortex (headline) or the forced isotropic "
                          "turbulence LES (force field, Cs = 0.1) on the same n^3 box")
-    ap.add_argument("--only", default=None, choices=["channel", "hit", "tgv", "adjoint"],
+    ap.add_argument("--only", default=None, choices=["channel", "hit", "tgv", "adjoint", "d2q9"],
                     help="run only this form (16-bit storage by --storage, shape by --shape) and print its "
                          "MLUPS; for profiling captures of one kernel variant")
     ap.add_argument("--shape", default=None, help="nx,ny,nz of the --only form")
@@ -712,6 +712,10 @@ def only_form(args):
         out["adjoint_step_frac_of_hbm"] = (out["adjoint_step_MLUPS"] * ADJOINT_SEGMENT_BYTES_PER_CELL / 1e3
                                            / peaks()[0]["hbm_gbs"])
         print(json.dumps({"form": "adjoint", "shape": [n, n, n], "storage": "f32", **out}))
+        return
+    if args.only == "d2q9":
+        out = run_poiseuille(cm, steps=args.form_steps)
+        print(json.dumps({"form": "d2q9", "shape": [64, 32, 1], "storage": "f64", **out}))
         return
     if args.only == "channel":
         nx, ny, nz = (int(v) for v in (args.shape or "1024,256,256").split(","))
