@@ -248,13 +248,8 @@ __global__ void __launch_bounds__(kBlock, CM_ADJ_MIN_BLOCKS) k_adjoint_step(cons
     }
 
     // ---- forward recomputation (plain central moments of fbar) ----
-    R A[Q];                                   // pull, then kbar
-    gather<D, S, WALLS>(state, x, y, z, p, A);
-    sfor<Q>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        constexpr R w = (R)weight<D>(i);
-        A[slot<D>(i)] += w;
-    });
+    R A[Q];                                   // pull (the populations fbar), then kbar
+    gather<D, S, WALLS, false, kPullFull>(state, x, y, z, p, A);
     R F[3];
     load_force<R>(Ff, p, cell, F);
     // rho and sum g e: the e = 0 terms are left out (a product by zero is not removed by the

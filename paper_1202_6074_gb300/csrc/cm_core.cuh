@@ -409,9 +409,11 @@ template <class R> __device__ __forceinline__ R wall_factor(int cnt) {
 
 // ------------------------------------------------------------------------------------------
 // Pull with periodic wrap and half-way bounce-back; fills h (slot order) with the deviation
-// populations h = w d, or with WEIGHTED = false the stored deviations d themselves
+// populations h = w d (kPullDev), the stored deviations d themselves (kPullStored), or the
+// populations fbar = w (1 + d) (kPullFull)
 // ------------------------------------------------------------------------------------------
-template <int D, class S, bool WALLS, bool BIG = false, bool WEIGHTED = true>
+enum { kPullStored = 0, kPullDev = 1, kPullFull = 2 };
+template <int D, class S, bool WALLS, bool BIG = false, int PULL = kPullDev>
 __device__ __forceinline__ void gather_impl(const S* __restrict__ src, int x, int y, int z, const PR<typename Codec<S>::R>& p,
                                        typename Codec<S>::R (&h)[Lat<D>::Q]) {
     using R = typename Codec<S>::R;
@@ -473,10 +475,10 @@ __device__ __forceinline__ void gather_impl(const S* __restrict__ src, int x, in
                 if constexpr (c != 1) eu = bz ? eu + e_dot<D, i>(p.uw[2][sz]) : eu;
                 d = fma(wall_factor<R>((int)bx + (int)by + (int)bz), eu, d);
             }
-            h[slot<D>(i)] = WEIGHTED ? d * w : d;
+            h[slot<D>(i)] = PULL == kPullStored ? d : PULL == kPullDev ? d * w : fma(d, w, w);
         } else {
             const R d = Codec<S>::ld(src + (IX(i) * PS + row[c][b] + (unsigned)xs[a]));
-            h[slot<D>(i)] = WEIGHTED ? d * w : d;
+            h[slot<D>(i)] = PULL == kPullStored ? d : PULL == kPullDev ? d * w : fma(d, w, w);
         }
     });
 }
@@ -485,16 +487,16 @@ __device__ __forceinline__ void gather_impl(const S* __restrict__ src, int x, in
 // or last layer of a bounce-back axis); everywhere else the periodic pull, which never leaves the
 // box on a wall axis there. With x-rows per warp, y and z are warp-uniform, so the branch only
 // diverges on x walls.
-template <int D, class S, bool WALLS, bool BIG = false, bool WEIGHTED = true>
+template <int D, class S, bool WALLS, bool BIG = false, int PULL = kPullDev>
 __device__ __forceinline__ void gather(const S* __restrict__ src, int x, int y, int z, const PR<typename Codec<S>::R>& p,
                                        typename Codec<S>::R (&h)[Lat<D>::Q]) {
     if constexpr (WALLS) {
         const bool near = (p.bc[0] == 1 && (x == 0 || x == p.nx - 1)) || (p.bc[1] == 1 && (y == 0 || y == p.ny - 1)) ||
                           (D == 3 && p.bc[2] == 1 && (z == 0 || z == p.nz - 1));
-        if (near) gather_impl<D, S, true, BIG, WEIGHTED>(src, x, y, z, p, h);
-        else gather_impl<D, S, false, BIG, WEIGHTED>(src, x, y, z, p, h);
+        if (near) gather_impl<D, S, true, BIG, PULL>(src, x, y, z, p, h);
+        else gather_impl<D, S, false, BIG, PULL>(src, x, y, z, p, h);
     } else {
-        gather_impl<D, S, false, BIG, WEIGHTED>(src, x, y, z, p, h);
+        gather_impl<D, S, false, BIG, PULL>(src, x, y, z, p, h);
     }
 }
 

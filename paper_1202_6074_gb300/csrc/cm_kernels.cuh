@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S>()) k_step(const S* 
     const unsigned cell = (unsigned)((z * p.ny + y) * p.nx + x);
     const IX PS = plane_stride<FT::BIG>(p);
     R h[Q];
-    gather<D, S, FT::WALLS, FT::BIG, false>(src, x, y, z, p, h);
+    gather<D, S, FT::WALLS, FT::BIG, kPullStored>(src, x, y, z, p, h);
     R F[3];
     load_force<R, FT::FIELD, FT::BIG>(Ff, p, cell, F);
     // the collision returns the stored deviations (inverse weights folded into its last sweep)
