@@ -7,9 +7,12 @@ factor, a wrong Maxwellian moment, central moments about the wrong velocity, a t
 stream, swapped third/fourth-order rates, a wrong eddy-viscosity
 constant, a flipped moving-wall term, an initial state without its -S/2 term, 3D factorized
 attractors built over the wrong axes, divided by one power of rho too many, from the
-pre-collision second-order moments, or non-zero where a factor vanishes, and in the turbulence closure an eddy stress without its
-factor 2, an unsymmetrised strain rate and a van Driest wall distance without the half cell.
+pre-collision second-order moments, or non-zero where a factor vanishes, in the turbulence closure an eddy stress without its
+factor 2, an unsymmetrised strain rate and a van Driest wall distance without the half cell,
+reduced compressibility ignored in the velocity, the trace relaxed with the shear rate, and a
+storage emulation that truncates the deviations or rounds the populations themselves.
 """
+import dataclasses
 import inspect
 import os
 
@@ -21,15 +24,18 @@ import test_oracle_collision as TC
 import test_oracle_filtered as TFI
 import test_oracle_flows as TF
 import test_oracle_les as TL
+import test_oracle_storage as TS
 from oracle import collision as C
 from oracle import filtered as FL
 from oracle import les as L
 from oracle import moments as M
+from oracle import solver as SV
 from oracle import stream as ST
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 SLOW = {"test_poiseuille_exact_with_magic_parameter", "test_poiseuille_default_rates_wall_error_is_small",
-        "test_couette_exact", "test_galilean_invariance_of_taylor_green_decay"}
+        "test_couette_exact", "test_galilean_invariance_of_taylor_green_decay",
+        "test_storage_error_scales_with_the_unit_roundoff"}
 
 
 def _calls(module, include_slow=()):
@@ -60,7 +66,7 @@ def _calls(module, include_slow=()):
 def _failures(include_slow=(), first=False):
     """Names of the pins that fail (only the first one with first=True)."""
     failed = []
-    for mod in (TB, TC, TF, TL, TFI):
+    for mod in (TB, TC, TF, TL, TFI, TS):
         for name, thunk in _calls(mod, include_slow):
             try:
                 thunk()
@@ -139,9 +145,49 @@ MUTATIONS = {
                                                                       _wrong_axes((2, 1, 1), (2, 0, 0), (1, 1, 0))),
     "factorized (1,2,1) with the wrong diagonal": lambda mp: _wrap(mp, C, "_factorized_attractor",
                                                                   _wrong_axes((1, 2, 1), (2, 0, 0), (1, 0, 1))),
+    "reduced compressibility ignored (u = j / rho)": lambda mp: _wrap(mp, C, "hydrodynamics", _without_reduced),
+    "trace relaxed with the shear rate": lambda mp: _wrap(mp, C, "collide", _bulk_as_shear),
+    "stored deviations truncated instead of rounded": lambda mp: mp.setattr(SV, "round_to_storage", _truncated_storage),
+    "stored populations rounded instead of their deviations": lambda mp: mp.setattr(SV, "round_to_storage",
+                                                                                   _rounded_populations),
     "factorized (2,2,1) not zero": lambda mp: _wrap(mp, C, "_factorized_attractor",
                                                     _wrong_axes((2, 2, 1), (2, 0, 0), (0, 1, 1))),
 }
+
+
+def _without_reduced(f):
+    """The velocity j / rho even where reduced compressibility asks for j / rho0."""
+    def g(fbar, F, lat, p=None):
+        if p is not None and p.reduced_compressibility:
+            p = dataclasses.replace(p, reduced_compressibility=False)
+        return f(fbar, F, lat, p)
+    return g
+
+
+def _bulk_as_shear(f):
+    """The trace of the second-order moments relaxed with the shear rate, whatever omega_bulk says."""
+    def g(fbar, F, lat, p, cs_eff=None):
+        return f(fbar, F, lat, dataclasses.replace(p, omega_bulk=0.0), cs_eff)
+    return g
+
+
+def _truncated_storage(s, w, storage):
+    """Deviations cut toward zero to the storage type's precision (the low bits of the float32
+    pattern dropped) instead of rounded to nearest."""
+    if storage in (None, "f64"):
+        return s
+    wv = w.view(-1, *([1] * (s.dim() - 1)))
+    cut = {"bf16": 16, "f16": 13, "f32": 0}[storage]
+    d = (s / wv - 1.0).to(torch.float32)
+    d = (d.view(torch.int32) & -(1 << cut)).view(torch.float32).to(torch.float64)
+    return wv * (1.0 + d)
+
+
+def _rounded_populations(s, w, storage):
+    """The populations f themselves rounded to the storage type instead of their deviations d."""
+    if storage in (None, "f64"):
+        return s
+    return s.to(SV.STORAGE_DTYPES[storage]).to(torch.float64)
 
 
 def _extra_rho(f):

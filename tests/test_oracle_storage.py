@@ -16,9 +16,9 @@ import numpy as np
 import pytest
 import torch
 
+import oracle.solver as SV
 from oracle.collision import Params
 from oracle.lattice import get as get_lattice
-from oracle.solver import OracleSim, round_to_storage
 from paper_1202_6074_gb300 import workloads as W
 
 
@@ -78,7 +78,7 @@ def test_round_to_storage_is_the_nearest_value_ties_to_even(storage):
     x = np.concatenate([x, mids, exact])
     want = _nearest_even(x, vals, even)
     w = torch.ones(1, dtype=torch.float64)
-    got = round_to_storage(torch.tensor(1.0 + x).view(1, -1), w, storage).view(-1).numpy() - 1.0
+    got = SV.round_to_storage(torch.tensor(1.0 + x).view(1, -1), w, storage).view(-1).numpy() - 1.0
     # 1 + x is exact in float64 for every x above (at most 24 significant bits, |x| < 1)
     assert np.array_equal(got, want), np.flatnonzero(got != want)[:10]
 
@@ -86,15 +86,15 @@ def test_round_to_storage_is_the_nearest_value_ties_to_even(storage):
 def test_round_to_storage_fp64_and_none_are_identity():
     s = torch.rand(27, 3, 4, 5, dtype=torch.float64)
     w = get_lattice("D3Q27").w
-    assert torch.equal(round_to_storage(s, w, None), s)
-    assert torch.equal(round_to_storage(s, w, "f64"), s)
+    assert torch.equal(SV.round_to_storage(s, w, None), s)
+    assert torch.equal(SV.round_to_storage(s, w, "f64"), s)
 
 
 def _tgv_error(storage, background, n=10, steps=40):
     rho, u = W.taylor_green(n, n, n, u0=0.05, background=background)
     res = {}
     for st in (None, storage):
-        o = OracleSim("D3Q27", n, n, n, Params(tau=0.55), storage=st)
+        o = SV.OracleSim("D3Q27", n, n, n, Params(tau=0.55), storage=st)
         o.init(torch.tensor(rho), torch.tensor(u))
         o.step(steps)
         res[st] = o.moments()[1]
