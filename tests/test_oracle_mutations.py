@@ -9,8 +9,9 @@ constant, a flipped moving-wall term, an initial state without its -S/2 term, 3D
 attractors built over the wrong axes, divided by one power of rho too many, from the
 pre-collision second-order moments, or non-zero where a factor vanishes, in the turbulence closure an eddy stress without its
 factor 2, an unsymmetrised strain rate and a van Driest wall distance without the half cell,
-reduced compressibility ignored in the velocity, the trace relaxed with the shear rate, and a
-storage emulation that truncates the deviations or rounds the populations themselves.
+reduced compressibility ignored in the velocity, the trace relaxed with the shear rate, a
+storage emulation that truncates the deviations or rounds the populations themselves, a halved
+moving-wall term, an inverse transform about zero velocity and a source with F instead of F/rho.
 """
 import dataclasses
 import inspect
@@ -128,7 +129,14 @@ MUTATIONS = {
     "moving-wall term flipped": lambda mp: _wrap(
         mp, ST, "_wall_terms",
         lambda f: lambda lat, i, shape, bc, uw, sign: (lambda m, w: (m, -w))(*f(lat, i, shape, bc, uw, sign))),
+    "moving-wall term halved": lambda mp: _wrap(
+        mp, ST, "_wall_terms",
+        lambda f: lambda lat, i, shape, bc, uw, sign: (lambda m, w: (m, 0.5 * w))(*f(lat, i, shape, bc, uw, sign))),
     "initial state without -S/2": lambda mp: _wrap(mp, C, "equilibrium", lambda f: lambda rho, u, F, lat: f(rho, u, 0 * F, lat)),
+    "inverse transform about zero velocity": lambda mp: _wrap(
+        mp, M, "central_to_populations", lambda f: lambda kappa, u, lat: f(kappa, 0 * u, lat)),
+    "source with F instead of F / rho": lambda mp: _wrap(
+        mp, C, "source_central", lambda f: lambda kbar, rho, F, lat: f(kbar, rho, F * rho, lat)),
     "eddy stress without its factor 2": lambda mp: _wrap(
         mp, FL, "eddy_stress", lambda f: lambda u, cs, d: {k: 0.5 * v for k, v in f(u, cs, d).items()}),
     "strain rate not symmetrised": lambda mp: mp.setattr(
