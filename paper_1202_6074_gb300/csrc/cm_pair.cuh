@@ -59,6 +59,16 @@ template <class S, class FT> constexpr bool pair_adjacent() { return sizeof(S) =
 // bound by HBM, keep the product at the store.
 template <class S, class FT> __host__ __device__ constexpr bool pair_dev() { return sizeof(S) == 2; }
 
+// Blocks of kBlock threads whose x extent divides the pair threads of a row (a multiple of 32:
+// nx is a multiple of 64 on this kernel), so that no block is left partly idle at the end of a
+// row: 128 x 1 where it divides, else 64 x 2 or 32 x 4 (nx = 384 or 576: 25 % of the threads
+// idle with 128-wide blocks).
+inline dim3 pair_block(int half) {
+    int bx = kBlock;
+    while (bx > 32 && half % bx != 0) bx /= 2;
+    return dim3(bx, kBlock / bx, 1);
+}
+
 // Plane ring of the two-steps-per-pass schedule (launch_pair_two_steps): the intermediate state
 // t+1 lives in a small buffer of z-planes instead of a full state buffer. Plane z sits in slot
 // z for z < 2 (kept until the end of the pass: the periodic wrap reads them last) and in slot
@@ -334,7 +344,7 @@ __global__ void __launch_bounds__(kBlock, pair_min_blocks<S, FT>()) k_step_pair(
 template <class S, class FT>
 void launch_pair(const void* src, void* dst, const void* Ff, const Params& p, cudaStream_t st) {
     const int half = p.nx / 2;
-    const dim3 b = cell_block(half);
+    const dim3 b = pair_block(half);
     const dim3 g((half + b.x - 1) / b.x, (p.ny + b.y - 1) / b.y, step_planes(p));
     Ring planes{};
     planes.z0 = p.z0;
