@@ -95,6 +95,9 @@ typedef struct cmlbm cmlbm_t;
  *                         (paper silent on the model; frame invariance required by Sec. 1):
  *                         Pi = kappa_ij - c_s^2 rho delta_ij from second-order central moments,
  *                         Q = |Pi|, tau_eff = (tau + sqrt(tau^2 + 18 sqrt(2) C^2 Q / rho)) / 2.
+ *                         With FP32 arithmetic (FP32 and 16-bit storage) the two square roots
+ *                         and 1 / tau_eff use the hardware approximations (within a few ulp);
+ *                         FP64 storage uses the rounded operations.
  *   van_driest_aplus      A+ of the damping C = C_s (1 - exp(-y+/A+)); 0 disables. Needs y walls.
  *   van_driest_utau_over_nu  u_tau / nu_0 so that y+ = y_wall * u_tau / nu_0, y_wall = distance to
  *                         the nearest y wall (j + 1/2 or ny - 1/2 - j).
